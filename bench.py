@@ -1,0 +1,484 @@
+"""Benchmark of the UBS differentiable rasterizer on GB300.
+
+Workload (one step = one pass of the whole path over one batch): the static
+N=3 scene of 1,000,000 primitives (64-cluster Gaussian mixture in [-5,5]^3)
+seen by one 1600x1060 camera on a radius-8 sphere: preprocess -> bin_sort ->
+render_fwd -> render_bwd (blend backward + parameter backward), dL/dimage of
+an L1 loss against a uniform-random target precomputed once.  Metric:
+forward+backward megapixels per second (and views per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank renders its own camera of the same scene
+(weak scaling, no collective on the data path); the elapsed time is the
+maximum over ranks.  ``--impl reference`` times the CPU oracle (float64
+reference renderer) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd megapixels/sec and views/sec at 1 GB300, batched vs per-view; % of roofline"
+L2_BYTES = 129 * 2 ** 20
+
+# per-pair algorithmic work of the blend kernels (FP32 lane operations; the
+# MUFU operations are bounded separately, see the design notes)
+FWD_FP32_PER_PAIR, FWD_MUFU_PER_PAIR = 16, 2
+BWD_FP32_PER_PAIR, BWD_MUFU_PER_PAIR = 45, 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--primitives", type=int, default=1_000_000)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched vs per-view comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank, P):
+    from paper_2510_03312_gb300 import scenes as S
+
+    wl = S.workload_static_large(P=P)
+    if rank > 0:  # weak scaling: another camera of the same scene per rank
+        rng = np.random.default_rng(1000 + rank)
+        wl.views = S.sphere_views(rng, 1, 8.0, 1600, 1060)
+    return wl
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# our implementation
+# ----------------------------------------------------------------------------
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tops(n_sm, sm_mhz):
+    """FP32 lane-operation peak (128 FP32 lanes per SM per clock).  The MUFU
+    pipe (16 per SM per clock) allows 8 FP32 operations per MUFU operation;
+    for the backward blend (45 FP32 : 3 MUFU) and the forward blend (16 : 2)
+    the FP32 pipe is the binding one or tied, so the ALU peak is the FP32
+    lane rate."""
+    return n_sm * 128 * sm_mhz * 1e6 / 1e12
+
+
+def source_sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2510_03312_gb300", "csrc", d["source"])
+    if source_sha(src) != d["source_sha"]:
+        return None
+    return d["dram_bytes_per_launch"]
+
+
+def kernels_per_step(r):
+    """Kernels of this library launched by one step (memsets excluded)."""
+    V, S = len(r.views), len(r.scenes)
+    NT = sum(((v.width + r.cfg.tile_w - 1) // r.cfg.tile_w) * ((v.height + r.cfg.tile_h - 1) // r.cfg.tile_h)
+             for v in r.views)
+    bits = max(0, math.ceil(math.log2(NT))) if NT > 1 else 0
+    tile_passes = (bits + 7) // 8
+    upload = (V + 15) // 16
+    pre = upload + S
+    sort = 1 + 4 + 1 + 1 + tile_passes
+    return pre + sort + 1 + 1 + S
+
+
+def bench_ours(args, rank, world, local):
+    import torch
+
+    from paper_2510_03312_gb300 import build as B
+    from paper_2510_03312_gb300 import raster
+    from paper_2510_03312_gb300 import scenes as S
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = workload(rank, args.primitives)
+    sc = wl.scenes[0]
+    ds = raster.DeviceScene.from_scene(sc, device=dev)
+    r = raster.Rasterizer([ds], wl.views, wl.cfg, device=dev)
+    img = r.forward(check=True)  # sizes the instance capacity (one sync)
+    st = r.status()
+    # dL/dimage of mean |image - target|
+    target = r.pack(S.l1_target(1, wl.views))
+    dL = (torch.sign(img - target) / img.numel()).contiguous()
+    torch.cuda.synchronize()
+    # pair count (diagnostic kernel variant, outside the timed region)
+    r.problem.cfg.flags |= 2
+    r.render_fwd()
+    pairs = int(r.export(9).to(torch.int64).sum().item())
+    r.problem.cfg.flags &= ~2
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    names = ["preprocess", "bin_sort", "render_fwd", "render_bwd_blend", "render_bwd_params"]
+
+    def step(evs):
+        evs[0].record(stream)
+        r.preprocess()
+        evs[1].record(stream)
+        r.bin_sort()
+        evs[2].record(stream)
+        r.render_fwd()
+        evs[3].record(stream)
+        r.render_bwd_blend(dL)
+        evs[4].record(stream)
+        r.render_bwd_params()
+        evs[5].record(stream)
+
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        step([ev() for _ in range(6)])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    all_evs = []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_((i + 7) & 0xFF)
+        evs = [ev() for _ in range(6)]
+        step(evs)
+        all_evs.append(evs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(5)] for e in all_evs])  # ms
+    step_ms = stage.sum(1)
+    total_ms = float(step_ms.sum())
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    mp_per_view = wl.views[0].width * wl.views[0].height / 1e6
+    value = world * args.steps * mp_per_view / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    # roofline of the dominant kernel
+    stage_mean = stage.mean(0)
+    dom = int(np.argmax(stage_mean))
+    pk, pk_src = peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    ops_per_pair = {"render_fwd": FWD_FP32_PER_PAIR, "render_bwd_blend": BWD_FP32_PER_PAIR}
+    roof = {}
+    if names[dom] in ops_per_pair:
+        ach = ops_per_pair[names[dom]] * pairs / (stage_mean[dom] * 1e-3) / 1e12
+        peak = alu_peak_tops(n_sm, pk.get("sm_max_mhz", 2070.0))
+        kern = "render_bwd_blend" if names[dom] == "render_bwd_blend" else "render_fwd"
+        roof = {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic_record(kern),
+                "work": f"{ops_per_pair[names[dom]]} FP32 lane-ops per pair x {pairs} pairs",
+                "peak_source": f"152 SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                               f"(clock of {pk_src} peaks file)"}
+    else:
+        nbytes = {"preprocess": 60 * sc.P + 44 * sc.P}.get(names[dom])
+        if nbytes:
+            ach = nbytes / (stage_mean[dom] * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": names[dom], "achieved": round(ach, 1),
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
+                    "traffic": traffic_record(names[dom])}
+    # end to end through the public API with host buffers
+    e2e = bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "primitives": sc.P, "views": len(wl.views),
+                   "width": wl.views[0].width, "height": wl.views[0].height,
+                   "tile": f"{wl.cfg.tile_w}x{wl.cfg.tile_h}", "parallelism": f"replicas x{world}",
+                   "l2": "flushed (2x L2 buffer written) between timed steps",
+                   "instances": int(st.instances), "visible_records": int(st.visible_records),
+                   "pairs": pairs},
+        "views_per_sec": round(world * args.steps / (total_ms / 1e3), 2),
+        "stage_ms": {n: round(float(m), 4) for n, m in zip(names, stage_mean)},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": kernels_per_step(r) * args.steps,
+        "clocks": clk,
+        "wall_s_timed_loop": round(wall, 3),
+    }
+    if rank == 0 and not args.no_batched and world == 1:
+        out["batched"] = bench_batched(dev)
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view):
+    """Same metric through the public API (Rasterizer.forward/backward) with
+    host buffers: every step copies the parameters and dL/dimage from pinned
+    host memory and reads the gradients and the image back."""
+    import torch
+
+    h_params = ds.params.cpu().pin_memory()
+    h_dL = dL.cpu().pin_memory()
+    h_grad = torch.empty_like(ds.params, device="cpu").pin_memory()
+    h_img = torch.empty_like(r.image, device="cpu").pin_memory()
+    stream = torch.cuda.current_stream()
+    d_dL = torch.empty_like(dL)
+
+    def step():
+        ds.params.copy_(h_params, non_blocking=True)
+        d_dL.copy_(h_dL, non_blocking=True)
+        img = r.forward(check=False)
+        g = r.backward(d_dL)[0]
+        h_img.copy_(img, non_blocking=True)
+        h_grad.copy_(g, non_blocking=True)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bi = h_params.numel() * 4 + h_dL.numel() * 4
+    bo = h_grad.numel() * 4 + h_img.numel() * 4
+    return {"value": round(world * args.steps * mp_per_view / (ms / 1e3), 2), "unit": "MP/s",
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": round(ms / args.steps, 4)}
+
+
+def bench_batched(dev, steps=10, warmup=3):
+    """View-dependent (N=6, 500K, 16 x 1280x720) and dynamic (N=7, 300K,
+    8 x 1352x1014) workloads: all views in one problem against one problem
+    per view launched back to back, forward+backward."""
+    import torch
+
+    from paper_2510_03312_gb300 import raster
+    from paper_2510_03312_gb300 import scenes as S
+
+    res = {}
+    for wl in (S.workload_view_dependent(), S.workload_dynamic()):
+        ds = raster.DeviceScene.from_scene(wl.scenes[0], device=dev)
+        mp = sum(v.width * v.height for v in wl.views) / 1e6
+        batched = raster.Rasterizer([ds], wl.views, wl.cfg, device=dev)
+        singles = [raster.Rasterizer([ds], [v], wl.cfg, device=dev) for v in wl.views]
+        out = {}
+        for mode, rs in (("batched", [batched]), ("per_view", singles)):
+            dls = []
+            for r in rs:
+                img = r.forward(check=True)
+                dls.append(torch.full_like(img, 1.0 / img.numel()))
+            torch.cuda.synchronize()
+
+            def step():
+                for r, d in zip(rs, dls):
+                    r.forward(check=False)
+                    r.backward(d)
+
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            out[mode] = {"ms_per_step": round(ms, 4), "MP_per_s": round(mp / (ms / 1e3), 2),
+                         "views_per_s": round(len(wl.views) / (ms / 1e3), 2)}
+        out["speedup_batched"] = round(out["per_view"]["ms_per_step"] / out["batched"]["ms_per_step"], 3)
+        res[wl.name] = out
+        del batched, singles
+        torch.cuda.empty_cache()
+    return res
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(P, n_tiles=24, seed=0):
+    """Times the float64 oracle on a bounded sample of the workload: every
+    primitive's float32 decision stage and float64 conditioning/projection
+    (forward and autograd backward), plus the compositing forward+backward of
+    n_tiles tiles; the tile part is scaled to the whole image."""
+    import torch
+
+    from oracle import render64 as R64
+
+    wl = workload(0, P)
+    t0 = time.perf_counter()
+    orc = R64.Oracle(wl.scenes, wl.views, wl.cfg)
+    counts = np.diff(orc.bins["ranges"], axis=1)[:, 0]
+    rng = np.random.default_rng(seed)
+    tiles = sorted(rng.choice(counts.size, n_tiles, replace=False).tolist())
+    t1 = time.perf_counter()
+    leaves = orc.leaves(True)
+    recs = orc.records(leaves)
+    t2 = time.perf_counter()
+    out = orc.render(leaves=leaves, tiles=tiles, recs=recs)
+    img = out["image"][0]
+    m = ~torch.isnan(img)
+    loss = torch.where(m, img, torch.zeros_like(img)).abs().sum()
+    t3 = time.perf_counter()
+    loss.backward()
+    t4 = time.perf_counter()
+    n_total = counts.size
+    # backward time splits between records and tiles; attribute it by tile share
+    t_prim = (t1 - t0) + (t2 - t1)
+    t_tiles = (t3 - t2) + (t4 - t3)
+    full = t_prim + t_tiles * n_total / n_tiles
+    mp = wl.views[0].width * wl.views[0].height / 1e6
+    return {"value": round(mp / full, 5), "unit": "MP/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"all {wl.scenes[0].P} primitives (float32 stage + float64 conditioning/projection) and "
+                      f"forward+backward compositing of {n_tiles} of {n_total} tiles, tile time scaled to the "
+                      f"whole 1600x1060 view",
+            "seconds": round(t4 - t0, 2), "extrapolated_s_per_step": round(full, 2)}
+
+
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return None
+    steps = []
+    for i in range(args.warmup):
+        oracle_sample(args.primitives, n_tiles=4, seed=100 + i)
+    for i in range(args.steps):
+        steps.append(oracle_sample(args.primitives, n_tiles=24, seed=i))
+    v = float(np.mean([s["value"] for s in steps]))
+    s0 = steps[0]
+    wl_name = workload(0, 8).name
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "MP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * s0["extrapolated_s_per_step"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "static_n3_1m_1600x1060", "primitives": args.primitives,
+                                            "views": 1, "width": 1600, "height": 1060},
+            "cpu_baseline": {"value": round(v, 5), "unit": "MP/s", "cores": s0["cores"], "kind": "oracle",
+                             "sample": s0["sample"]},
+            "e2e": {"value": round(v, 5), "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = bench_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    # the CPU baseline runs first, in this process before any CUDA work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(args.primitives, n_tiles=160)
+    out = bench_ours(args, rank, world, local)
+    if rank == 0:
+        out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * ubs.h -- C-ABI of the Universal Beta Splatting differentiable rasterizer
+ * (arXiv 2510.03312) for NVIDIA GB300 (sm_103a).
+ *
+ * The library renders N-dimensional anisotropic Beta kernels (N = 3, 4, 6, 7:
+ * 3 spatial dimensions plus C = N - 3 query dimensions, time and/or view
+ * direction) and differentiates the rendering.  Each entry point is one step
+ * of the path:
+ *
+ *   ubs_preprocess  kernel construction (Sec. 4.2), Beta-modulated
+ *                   conditioning on each view's query (Sec. 4.3, 4.4) and EWA
+ *                   projection with the compact Beta support (Sec. 3)
+ *   ubs_bin_sort    tile binning and the front-to-back depth order
+ *                   ("standard splatting", Sec. 4.5; ordering of Sec. 3)
+ *   ubs_render_fwd  per-tile front-to-back alpha compositing (Sec. 3)
+ *   ubs_render_bwd  gradients of the rendered images with respect to every
+ *                   primitive parameter (differentiable rendering, Sec. 4.5)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Memory: every pointer in ubs_scene, ubs_scene_grad, the image and dL/dimage
+ *   arguments and the workspace is a DEVICE pointer owned by the caller.  The
+ *   ubs_problem, ubs_scene/ubs_scene_grad and ubs_view arrays themselves are
+ *   HOST memory, read during the call only.  The library allocates nothing
+ *   and frees nothing.
+ * Streams: every call is asynchronous on `stream`; nothing synchronises
+ *   except ubs_read_status.  The sequence preprocess -> bin_sort ->
+ *   render_fwd -> render_bwd on one workspace must be issued in that order on
+ *   one stream (or with equivalent dependencies); it can be captured in a
+ *   CUDA graph.
+ * Workspace: all state between calls lives in the caller's workspace of at
+ *   least ubs_workspace_size(problem) bytes, 256-byte aligned.  Calls of the
+ *   same problem on different workspaces may run concurrently.
+ * Errors: argument errors (null pointers, unsupported N, misalignment, a
+ *   workspace that is too small) are returned synchronously and nothing is
+ *   launched.  Errors found on the device (instance capacity exceeded, a
+ *   bounded wait that gave up) are recorded in the workspace and reported by
+ *   ubs_read_status; kernels never trap.
+ * Floating point: parameters and images are IEEE binary32.
+ */
+#ifndef UBS_H
+#define UBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cudaStream_t; /* the CUDA runtime's stream handle */
+
+typedef enum {
+  UBS_OK = 0,
+  UBS_ERR_INVALID_ARG = 1, /* null pointer, bad size, unsupported N or mode */
+  UBS_ERR_ALIGNMENT = 2,   /* a pointer or the workspace is misaligned */
+  UBS_ERR_CAPACITY = 3,    /* more tile instances than instance_capacity */
+  UBS_ERR_CUDA = 4,        /* a CUDA launch or copy failed */
+  UBS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  UBS_ERR_INTERNAL = 6,
+  UBS_ERR_WORKSPACE = 7    /* workspace smaller than ubs_workspace_size */
+} ubs_status;
+
+enum { UBS_ROT_QUAT = 0, UBS_ROT_SKEW1 = 1 };
+
+enum {
+  UBS_FLAG_TIGHT_CUT = 1, /* cut each footprint at r_cut = 1-(a_min/o(q))^(1/beta_x) */
+  UBS_FLAG_COUNT_PAIRS = 2 /* diagnostic: ubs_render_fwd runs a variant that also counts,
+                              per pixel, the visited pairs with r < 1 (ubs_export 9) */
+};
+
+/* One primitive set (Sec. 4.1-4.3).  Structure of arrays: every block below
+ * is `rows` consecutive planes of P floats (plane r of a block starts at
+ * block + r * P).  All blocks are device pointers, 4-byte aligned.
+ *   mean_x  [3][P]        spatial mean mu_x
+ *   mean_q  [C][P]        query mean mu_q; rows ordered q = [t, d] (N=7),
+ *                         [d] (N=6), [t] (N=4); unused for N=3 (may be NULL)
+ *   rot     [4][P] quaternion (w,x,y,z), normalised inside (UBS_ROT_QUAT), or
+ *           [3][P] omega with R = I + A(omega) (UBS_ROT_SKEW1, Sec. 4.2)
+ *   scale_x [3][P]        spatial scales s_x > 0
+ *   L_qx    [3C][P]       C x 3 cross block, row-major: (k, j) at row 3k + j
+ *   L_q     [C(C+1)/2][P] lower-triangular query block, packed row-major:
+ *                         (i, j <= i) at row i(i+1)/2 + j; diagonal s_q > 0
+ *   b       [1+C][P]      Beta parameters b_x, b_q1..b_qC (beta_x = 4 e^b_x,
+ *                         beta_q = e^b_q)
+ *   opacity [P]           o in [0, 1]
+ *   rgb     [3][P]        colour                                          */
+typedef struct {
+  int32_t N;        /* 3, 4, 6 or 7 */
+  int32_t rot_mode; /* UBS_ROT_QUAT or UBS_ROT_SKEW1 */
+  int64_t P;        /* number of primitives, >= 0 */
+  const float* mean_x;
+  const float* mean_q;
+  const float* rot;
+  const float* scale_x;
+  const float* L_qx;
+  const float* L_q;
+  const float* b;
+  const float* opacity;
+  const float* rgb;
+} ubs_scene;
+
+/* Gradient buffers with the layout of ubs_scene (device pointers, 4-byte
+ * aligned).  ubs_render_bwd OVERWRITES them (it does not accumulate). */
+typedef struct {
+  float* mean_x;
+  float* mean_q;
+  float* rot;
+  float* scale_x;
+  float* L_qx;
+  float* L_q;
+  float* b;
+  float* opacity;
+  float* rgb;
+} ubs_scene_grad;
+
+/* A pinhole view (Sec. 3: viewing transform W and projection).  x_cam =
+ * R x_world + t with camera axes x right, y down, z forward; pixel (i, j)
+ * has its centre at (i + 0.5, j + 0.5); u = fx x/z + cx, v = fy y/z + cy.
+ * `time` is the temporal query of N = 4 and N = 7 scenes (Sec. 4.4);
+ * `scene_id` selects the primitive set the view renders. */
+typedef struct {
+  float R[9]; /* row-major */
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float time;
+  int32_t scene_id;
+} ubs_view;
+
+/* Rasterizer constants ("standard splatting", Sec. 4.5; 3DGS practice). */
+typedef struct {
+  int32_t tile_w, tile_h; /* 8x8, 16x16, 16x32 (w x h = 16 x 32) or 32x32 */
+  float alpha_min;        /* skip a pair when alpha < alpha_min (1/255) */
+  float alpha_max;        /* alpha = min(alpha_max, o(q) (1 - r)^beta_x) (0.99) */
+  float T_min;            /* stop before T (1 - alpha) < T_min (1e-4) */
+  float eps2d;            /* screen-space dilation added to Sigma' (0.3 px^2) */
+  float near_plane;       /* cull when camera-space z <= near_plane (0.2) */
+  float jac_clip;         /* Jacobian ray clamp, multiple of tan(fov/2) (1.3) */
+  float bg[3];            /* background colour */
+  int32_t flags;          /* UBS_FLAG_* */
+} ubs_config;
+
+/* The whole problem of one call sequence: n_scenes primitive sets and
+ * n_views views (each view renders scenes[views[v].scene_id]).  Records are
+ * numbered record_offset(v) + p, views in order; tiles are numbered
+ * tile_offset(v) + ty * tiles_x(v) + tx.  Images of all views are packed:
+ * view v occupies 3 * height * width floats starting at pixel_offset(v) * 3,
+ * planar [3][height][width]. */
+typedef struct {
+  const ubs_scene* scenes; /* host array [n_scenes] */
+  int32_t n_scenes;        /* 1 .. 64 */
+  const ubs_view* views;   /* host array [n_views] */
+  int32_t n_views;         /* 1 .. 256 */
+  ubs_config cfg;
+  int64_t instance_capacity; /* maximum (tile, record) instances */
+} ubs_problem;
+
+/* Device-side status read back by ubs_read_status. */
+typedef struct {
+  int32_t status;              /* ubs_status of the device-side work */
+  int32_t reserved;
+  int64_t visible_records;     /* records with a non-empty tile rectangle */
+  int64_t instances;           /* (tile, record) instances required */
+} ubs_device_status;
+
+/* Bytes of workspace the problem needs (0 on invalid arguments).  Pure host
+ * arithmetic. */
+size_t ubs_workspace_size(const ubs_problem* problem);
+
+/* P1-P3 of Sec. 4.2-4.4 and Sec. 3: for every (view, primitive) record,
+ * builds Sigma from the spatial-orthogonal Cholesky factor, conditions it on
+ * the view's query (Beta-modulated mean, covariance and opacity), projects
+ * it (mean, conic, depth) and computes its tile rectangle under the compact
+ * Beta support.  Also resets the workspace's device status. */
+ubs_status ubs_preprocess(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                          cudaStream_t stream);
+
+/* B1-B3: lists every (tile, record) instance, orders each tile's list front
+ * to back by (float32 depth, record index) and finds each tile's range.
+ * If the instances exceed problem->instance_capacity the device status
+ * becomes UBS_ERR_CAPACITY (with the required count) and the lists are left
+ * incomplete; later calls on this workspace then do nothing. */
+ubs_status ubs_bin_sort(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                        cudaStream_t stream);
+
+/* R1 (Sec. 3): per pixel, alpha = min(alpha_max, o(q) (1 - r)^beta_x) for
+ * r < 1, blended front to back into colour and transmittance; writes the
+ * packed images (device, float32, see ubs_problem) and keeps the per-pixel
+ * final transmittance and last contributor in the workspace. */
+ubs_status ubs_render_fwd(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                          float* image, cudaStream_t stream);
+
+/* G1-G2: given dL/dimage (device, packed like the images), writes dL/dparams
+ * of every scene into grads[0 .. n_scenes-1] (host array of device buffers,
+ * overwritten).  Must follow ubs_render_fwd on the same workspace. */
+ubs_status ubs_render_bwd(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                          const float* dL_dimage, const ubs_scene_grad* grads, cudaStream_t stream);
+
+/* G1 alone: the backward blend.  Accumulates dL/d(mu', conic, log2 o(q),
+ * beta_x, rgb) of every record into the workspace (zeroed first). */
+ubs_status ubs_render_bwd_blend(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                                const float* dL_dimage, cudaStream_t stream);
+
+/* G2 alone: chains the workspace's per-record screen gradients back to the
+ * parameters of every scene (grads overwritten).  ubs_render_bwd is
+ * ubs_render_bwd_blend followed by ubs_render_bwd_params. */
+ubs_status ubs_render_bwd_params(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                                 const ubs_scene_grad* grads, cudaStream_t stream);
+
+/* Synchronises `stream` and copies the device status into *out (host). */
+ubs_status ubs_read_status(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                           ubs_device_status* out, cudaStream_t stream);
+
+/* Copies internal per-record and per-instance arrays out of the workspace
+ * (for tests and diagnostics).  `what` selects: 0 = depth keys [R] u32,
+ * 1 = tiles_touched [R] u32, 2 = rectangles [R] x 2 u32 (x0|y0<<16,
+ * x1|y1<<16), 3 = render records [R] x 12 f32, 4 = sorted instance records
+ * [instances] u32, 5 = tile starts [tiles + 1] u32, 6 = final T [pixels]
+ * f32, 7 = last contributor [pixels] u32, 8 = per-record screen gradients
+ * [R] x 12 f32, 9 = visited pairs with r < 1 [pixels] u32 (written by the
+ * UBS_FLAG_COUNT_PAIRS variant of ubs_render_fwd).  `dst` is device memory of at least `dst_bytes`; returns the
+ * bytes needed in *bytes_needed. */
+ubs_status ubs_export(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
+                      int32_t what, void* dst, size_t dst_bytes, size_t* bytes_needed,
+                      cudaStream_t stream);
+
+const char* ubs_status_string(ubs_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UBS_H */

@@ -1,0 +1,120 @@
+// common.cuh -- types shared by the kernels and the C-ABI layer.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifndef UBS_HD
+#define UBS_HD __host__ __device__ __forceinline__
+#endif
+
+namespace ubs {
+
+constexpr int kMaxViews = 256;
+constexpr int kMaxScenes = 64;
+constexpr float kLn2f = 0x1.62e430p-1f;
+
+// View constants as the kernels see them (one per view, in the workspace).
+struct ViewDev {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t W, H;
+  float time;
+  int32_t scene;
+  int32_t tiles_x, tiles_y;
+  uint32_t tile_off;  // first global tile id of the view
+  uint32_t rec_off;   // first record of the view
+  uint32_t pix_off;   // first pixel of the view (images are packed)
+  uint32_t pad[3];
+};
+static_assert(sizeof(ViewDev) == 112, "ViewDev layout");
+
+struct CfgDev {
+  int32_t tw, th;
+  float amin, amax, tmin, eps, near_plane, clip;
+  float bg[3];
+  int32_t flags;
+};
+
+struct SceneDev {
+  const float* mean_x;
+  const float* mean_q;
+  const float* rot;
+  const float* scale_x;
+  const float* L_qx;
+  const float* L_q;
+  const float* b;
+  const float* opacity;
+  const float* rgb;
+  int32_t N, rot_mode;
+  int64_t P;
+};
+
+struct SceneGradDev {
+  float* mean_x;
+  float* mean_q;
+  float* rot;
+  float* scale_x;
+  float* L_qx;
+  float* L_q;
+  float* b;
+  float* opacity;
+  float* rgb;
+};
+
+// Device status block at the start of the workspace.
+struct Header {
+  uint32_t status;       // ubs_status of device-side work (0 = ok)
+  uint32_t pad0;
+  uint64_t n_visible;    // records with tiles_touched > 0
+  uint64_t n_inst;       // instances required
+  uint32_t ctr[32];      // dynamic tile counters, one per single-pass kernel
+};
+
+// Workspace layout, computed on the host from the problem.
+struct Layout {
+  int32_t V, S;
+  uint32_t R;       // records
+  uint32_t NT;      // tiles
+  uint32_t NPIX;    // pixels
+  uint32_t cap;     // instance capacity
+  int32_t tile_bits, tile_passes;
+  uint32_t n_cmp_tiles;   // compaction scan tiles
+  uint32_t n_emit_tiles;  // emission scan tiles
+  uint32_t n_rng_tiles;   // range scan tiles
+  uint32_t n_dsort_tiles; // onesweep tiles over records
+  uint32_t n_isort_tiles; // onesweep tiles over instances
+  size_t header, views, rec4, key, tiles, rect, g2d;
+  size_t ckA, cvA, ckB, cvB;
+  size_t ikA, ivA, ikB, ivB;
+  size_t tcount, tstart;
+  size_t scan_stat, sort_stat, ghist;
+  size_t Tfin, last, pairs;
+  size_t total;
+};
+
+// float record of one (view, primitive) for the blend kernels: 3 x float4
+//   [mu'_x hi, mu'_y hi, mu'_x lo, mu'_y lo]
+//   [conic a, conic b, conic c, log2 o(q)]
+//   [beta_x, r, g, b]
+// r = a dx^2 + 2 b dx dy + c dy^2 with dx = (px - hi_x) - lo_x.
+constexpr int kRecFloats = 12;
+// per-record screen-space gradient: 3 x float4
+//   [d mu'_x, d mu'_y, d a, d b] [d c, d log2 o(q), d beta_x, d r] [d g, d b, -, -]
+constexpr int kGradFloats = 12;
+
+// status flags of the single-pass (decoupled look-back) scans: top 2 bits
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagInc = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+constexpr uint32_t kFlagAgg32 = 1u << 30;
+constexpr uint32_t kFlagInc32 = 2u << 30;
+constexpr uint32_t kValMask32 = (1u << 30) - 1;
+
+// bounded waits: a look-back gives up after this many polls of one word
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+enum DevStatus : uint32_t { kDevOk = 0, kDevCapacity = 3, kDevTimeout = 5, kDevInternal = 6 };
+
+}  // namespace ubs

@@ -1,0 +1,84 @@
+// preprocess.cu -- P1-P3: kernel construction, Beta-modulated conditioning
+// and projection of every (view, primitive) record.
+//
+// Compiled with --fmad=false -prec-div=true -prec-sqrt=true -ftz=false so
+// that the float32 rule set of spec32.cuh holds (see prim_forward.cuh).
+//
+// One thread per primitive of one scene; the thread builds the view-
+// independent part once (Sigma blocks, Cholesky of Sigma_q, Sigma_q^{-1}
+// Sigma_qx, beta) and then loops over the scene's views, so each primitive's
+// parameters are read from HBM once per batch of views.  Parameter planes
+// are structure-of-arrays: a warp reads 32 consecutive floats per plane.
+#include "kernels.cuh"
+#include "prim_forward.cuh"
+
+namespace ubs {
+
+template <int C>
+__device__ __forceinline__ void load_prim(const SceneDev& sc, int64_t p, PrimIn<C>& in) {
+  const int64_t P = sc.P;
+  for (int i = 0; i < 3; ++i) in.mx[i] = __ldg(sc.mean_x + i * P + p);
+  const int nr = sc.rot_mode == 0 ? 4 : 3;
+  for (int i = 0; i < 4; ++i) in.rot[i] = i < nr ? __ldg(sc.rot + i * P + p) : 0.0f;
+  for (int i = 0; i < 3; ++i) in.s[i] = __ldg(sc.scale_x + i * P + p);
+  for (int i = 0; i < 1 + C; ++i) in.b[i] = __ldg(sc.b + i * P + p);
+  in.o = __ldg(sc.opacity + p);
+  if constexpr (C > 0) {
+    for (int i = 0; i < C; ++i) in.mq[i] = __ldg(sc.mean_q + i * P + p);
+    for (int i = 0; i < 3 * C; ++i) in.lqx[i] = __ldg(sc.L_qx + i * P + p);
+    for (int i = 0; i < C * (C + 1) / 2; ++i) in.lq[i] = __ldg(sc.L_q + i * P + p);
+  }
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList vl, const ViewDev* __restrict__ views,
+                                                         CfgDev cfg, float4* __restrict__ rec4,
+                                                         uint32_t* __restrict__ key, uint32_t* __restrict__ tiles,
+                                                         uint2* __restrict__ rect) {
+  extern __shared__ ViewDev s_views[];
+  for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= sc.P) return;
+  PrimIn<C> in;
+  load_prim<C>(sc, p, in);
+  PrimVI<C> vi;
+  prim_stage<C>(in, sc.rot_mode, vi);
+  const float cr = __ldg(sc.rgb + p), cg = __ldg(sc.rgb + sc.P + p), cb = __ldg(sc.rgb + 2 * sc.P + p);
+  for (int k = 0; k < vl.n; ++k) {
+    const ViewDev& v = s_views[k];
+    ViewOut o;
+    view_stage<C>(in, vi, v, cfg, o);
+    const uint32_t r = v.rec_off + (uint32_t)p;
+    tiles[r] = o.tiles;
+    if (o.valid) {
+      key[r] = __float_as_uint(o.depth);
+      rect[r] = make_uint2((uint32_t)o.tx0 | ((uint32_t)o.ty0 << 16), (uint32_t)o.tx1 | ((uint32_t)o.ty1 << 16));
+      rec4[3 * (size_t)r + 0] = make_float4(o.mu_hi[0], o.mu_hi[1], o.mu_lo[0], o.mu_lo[1]);
+      rec4[3 * (size_t)r + 1] = make_float4(o.conic[0], o.conic[1], o.conic[2], log2f(o.oq));
+      rec4[3 * (size_t)r + 2] = make_float4(vi.beta_x, cr, cg, cb);
+    }
+  }
+}
+
+cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const ViewDev* views, const CfgDev& cfg,
+                              const Layout& L, char* ws, cudaStream_t st) {
+  if (sc.P == 0 || vl.n == 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((sc.P + threads - 1) / threads);
+  const size_t smem = sizeof(ViewDev) * vl.n;
+  float4* rec4 = (float4*)(ws + L.rec4);
+  uint32_t* key = (uint32_t*)(ws + L.key);
+  uint32_t* tiles = (uint32_t*)(ws + L.tiles);
+  uint2* rect = (uint2*)(ws + L.rect);
+  switch (sc.N) {
+    case 3: preprocess_kernel<0><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
+    case 4: preprocess_kernel<1><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
+    case 6: preprocess_kernel<3><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
+    case 7: preprocess_kernel<4><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ubs

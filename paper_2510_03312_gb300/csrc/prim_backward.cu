@@ -1,0 +1,92 @@
+// prim_backward.cu -- G2: chain the per-record screen gradients back to the
+// primitive parameters (math in prim_backward.cuh).
+//
+// One thread per primitive of one scene; it rebuilds the view-independent
+// quantities once, walks the scene's views accumulating in registers, and
+// writes every parameter gradient once: no atomics and a deterministic sum
+// over views.
+#include "kernels.cuh"
+#include "prim_backward.cuh"
+
+namespace ubs {
+
+namespace {
+
+template <int C>
+__device__ __forceinline__ void load_prim_b(const SceneDev& sc, int64_t p, PrimIn<C>& in) {
+  const int64_t P = sc.P;
+  for (int i = 0; i < 3; ++i) in.mx[i] = __ldg(sc.mean_x + i * P + p);
+  const int nr = sc.rot_mode == 0 ? 4 : 3;
+  for (int i = 0; i < 4; ++i) in.rot[i] = i < nr ? __ldg(sc.rot + i * P + p) : 0.0f;
+  for (int i = 0; i < 3; ++i) in.s[i] = __ldg(sc.scale_x + i * P + p);
+  for (int i = 0; i < 1 + C; ++i) in.b[i] = __ldg(sc.b + i * P + p);
+  in.o = __ldg(sc.opacity + p);
+  if constexpr (C > 0) {
+    for (int i = 0; i < C; ++i) in.mq[i] = __ldg(sc.mean_q + i * P + p);
+    for (int i = 0; i < 3 * C; ++i) in.lqx[i] = __ldg(sc.L_qx + i * P + p);
+    for (int i = 0; i < C * (C + 1) / 2; ++i) in.lq[i] = __ldg(sc.L_q + i * P + p);
+  }
+}
+
+template <int C>
+__global__ void __launch_bounds__(128) prim_backward_kernel(SceneDev sc, SceneGradDev gr, ViewList vl,
+                                                            const ViewDev* __restrict__ views, CfgDev cfg,
+                                                            const uint32_t* __restrict__ tiles,
+                                                            const float4* __restrict__ g2d) {
+  extern __shared__ ViewDev s_views[];
+  for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= sc.P) return;
+  PrimIn<C> in;
+  load_prim_b<C>(sc, p, in);
+  PrimVI<C> vi;
+  prim_stage<C>(in, sc.rot_mode, vi);
+  PrimAcc<C> acc;
+  acc_zero<C>(acc);
+  for (int k = 0; k < vl.n; ++k) {
+    const ViewDev& v = s_views[k];
+    const uint32_t r = v.rec_off + (uint32_t)p;
+    if (tiles[r] == 0) continue;
+    const float4 a = g2d[3 * (size_t)r], b = g2d[3 * (size_t)r + 1], c = g2d[3 * (size_t)r + 2];
+    const float g[10] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
+    prim_backward_view<C>(in, vi, v, cfg, g, acc);
+  }
+  PrimGrad<C> out;
+  prim_backward_final<C>(in, vi, sc.rot_mode, acc, out);
+  const int64_t P = sc.P;
+  for (int i = 0; i < 3; ++i) gr.mean_x[i * P + p] = out.mx[i];
+  const int nr = sc.rot_mode == 0 ? 4 : 3;
+  for (int i = 0; i < nr; ++i) gr.rot[i * P + p] = out.rot[i];
+  for (int i = 0; i < 3; ++i) gr.scale_x[i * P + p] = out.s[i];
+  for (int i = 0; i < 1 + C; ++i) gr.b[i * P + p] = out.b[i];
+  gr.opacity[p] = out.o;
+  for (int i = 0; i < 3; ++i) gr.rgb[i * P + p] = out.rgb[i];
+  if constexpr (C > 0) {
+    for (int i = 0; i < C; ++i) gr.mean_q[i * P + p] = out.mq[i];
+    for (int i = 0; i < 3 * C; ++i) gr.L_qx[i * P + p] = out.lqx[i];
+    for (int i = 0; i < C * (C + 1) / 2; ++i) gr.L_q[i * P + p] = out.lq[i];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_prim_backward(const SceneDev& sc, const SceneGradDev& g, const ViewList& vl, const ViewDev* views,
+                                 const CfgDev& cfg, const Layout& L, char* ws, cudaStream_t st) {
+  if (sc.P == 0) return cudaSuccess;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((sc.P + threads - 1) / threads);
+  const size_t smem = sizeof(ViewDev) * vl.n;
+  const uint32_t* tiles = (const uint32_t*)(ws + L.tiles);
+  const float4* g2d = (const float4*)(ws + L.g2d);
+  switch (sc.N) {
+    case 3: prim_backward_kernel<0><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
+    case 4: prim_backward_kernel<1><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
+    case 6: prim_backward_kernel<3><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
+    case 7: prim_backward_kernel<4><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ubs

@@ -1,0 +1,226 @@
+"""PyTorch plumbing around the C-ABI: device buffers, streams, autograd.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+rasterizer runs in ``libubs.so`` (see ``ubs.py``).  Nothing here computes any
+part of the method.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import ubs as U
+from .scenes import PLANE_ORDER, RasterConfig, Scene, View, plane_rows
+
+
+def config_struct(cfg: RasterConfig) -> U.ubs_config:
+    c = U.ubs_config()
+    c.tile_w, c.tile_h = int(cfg.tile_w), int(cfg.tile_h)
+    c.alpha_min, c.alpha_max, c.T_min = cfg.alpha_min, cfg.alpha_max, cfg.T_min
+    c.eps2d, c.near_plane, c.jac_clip = cfg.eps2d, cfg.near, cfg.jac_clip
+    c.bg[:] = [float(x) for x in cfg.bg]
+    c.flags = U.UBS_FLAG_TIGHT_CUT if cfg.tight_cut else 0
+    return c
+
+
+def view_struct(v: View) -> U.ubs_view:
+    s = U.ubs_view()
+    s.R[:] = [float(x) for x in np.asarray(v.R, np.float32).ravel()]
+    s.t[:] = [float(x) for x in np.asarray(v.t, np.float32).ravel()]
+    s.fx, s.fy, s.cx, s.cy = v.fx, v.fy, v.cx, v.cy
+    s.width, s.height, s.time, s.scene_id = v.width, v.height, v.time, v.scene_id
+    return s
+
+
+def _plane_ptrs(t: torch.Tensor, N: int, rot_mode: int):
+    """Device pointers of the plane blocks of a contiguous [K, P] tensor."""
+    P = t.shape[1]
+    base = t.data_ptr()
+    out, row = {}, 0
+    for name, rows in plane_rows(N, rot_mode).items():
+        out[name] = base + row * P * 4 if rows > 0 else None
+        row += rows
+    return out
+
+
+class DeviceScene:
+    """One primitive set on the GPU: ``params`` is a contiguous float32
+    [K, P] tensor with the plane order of ``scenes.PLANE_ORDER``."""
+
+    def __init__(self, N: int, rot_mode: int, params: torch.Tensor):
+        if params.dtype != torch.float32 or not params.is_cuda or not params.is_contiguous():
+            raise ValueError("params must be a contiguous float32 CUDA tensor")
+        self.N, self.rot_mode, self.params = N, rot_mode, params
+
+    @classmethod
+    def from_scene(cls, sc: Scene, device="cuda") -> "DeviceScene":
+        t = torch.from_numpy(np.ascontiguousarray(sc.params)).to(device)
+        return cls(sc.N, sc.rot_mode, t)
+
+    @property
+    def P(self) -> int:
+        return int(self.params.shape[1])
+
+    def struct(self) -> U.ubs_scene:
+        p = _plane_ptrs(self.params, self.N, self.rot_mode)
+        s = U.ubs_scene()
+        s.N, s.rot_mode, s.P = self.N, self.rot_mode, self.P
+        for name in PLANE_ORDER:
+            setattr(s, name, p[name])
+        return s
+
+    def grad_struct(self, g: torch.Tensor) -> U.ubs_scene_grad:
+        p = _plane_ptrs(g, self.N, self.rot_mode)
+        s = U.ubs_scene_grad()
+        for name in PLANE_ORDER:
+            setattr(s, name, p[name])
+        return s
+
+
+class Rasterizer:
+    """One problem (scenes, views, config) with its workspace and outputs.
+
+    ``forward`` runs preprocess -> bin_sort -> render_fwd on the current
+    stream and returns the packed images (views in order, each [3, H, W]);
+    ``backward`` runs render_bwd and returns one gradient tensor per scene,
+    shaped like the scene's params.
+    """
+
+    def __init__(self, scenes, views, cfg: RasterConfig, capacity: int | None = None, device="cuda"):
+        self.scenes = list(scenes)
+        self.views = list(views)
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self._scene_structs = (U.ubs_scene * len(self.scenes))(*[s.struct() for s in self.scenes])
+        self._view_structs = (U.ubs_view * len(self.views))(*[view_struct(v) for v in self.views])
+        self.problem = U.ubs_problem()
+        self.problem.scenes = self._scene_structs
+        self.problem.n_scenes = len(self.scenes)
+        self.problem.views = self._view_structs
+        self.problem.n_views = len(self.views)
+        self.problem.cfg = config_struct(cfg)
+        self.R = sum(self.scenes[v.scene_id].P for v in self.views)
+        self.pix_off = np.cumsum([0] + [v.width * v.height for v in self.views])
+        self.n_pix = int(self.pix_off[-1])
+        self._ws = None
+        self.ws_ptr, self.ws_bytes = None, 0
+        self.set_capacity(capacity if capacity is not None else max(4 * self.R, 1 << 16))
+        self.image = torch.empty(3 * self.n_pix, dtype=torch.float32, device=self.device)
+        self.grads = [torch.empty_like(s.params) for s in self.scenes]
+        self._grad_structs = (U.ubs_scene_grad * len(self.scenes))(
+            *[s.grad_struct(g) for s, g in zip(self.scenes, self.grads)])
+
+    # -- workspace
+    def set_capacity(self, cap: int):
+        cap = int(min(max(cap, 1), 0x7FFFFFFF))
+        self.problem.instance_capacity = cap
+        need = U.ubs_workspace_size(self.problem)
+        if need == 0:
+            raise ValueError("invalid problem (ubs_workspace_size returned 0)")
+        if self._ws is None or self.ws_bytes < need:
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+            base = self._ws.data_ptr()
+            self.ws_ptr = (base + 255) // 256 * 256
+            self.ws_bytes = need
+        self.capacity = cap
+
+    @staticmethod
+    def stream():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def _check(self, st, where):
+        if st != U.UBS_OK:
+            raise U.UBSError(st, where)
+
+    def status(self):
+        return U.ubs_read_status(self.problem, self.ws_ptr, self.ws_bytes, self.stream())
+
+    # -- steps
+    def preprocess(self):
+        self._check(U.ubs_preprocess(self.problem, self.ws_ptr, self.ws_bytes, self.stream()), "ubs_preprocess")
+
+    def bin_sort(self):
+        self._check(U.ubs_bin_sort(self.problem, self.ws_ptr, self.ws_bytes, self.stream()), "ubs_bin_sort")
+
+    def render_fwd(self, image=None):
+        image = self.image if image is None else image
+        self._check(U.ubs_render_fwd(self.problem, self.ws_ptr, self.ws_bytes, image.data_ptr(), self.stream()),
+                    "ubs_render_fwd")
+        return image
+
+    def render_bwd(self, dL_dimage: torch.Tensor):
+        dL = dL_dimage.contiguous()
+        self._check(U.ubs_render_bwd(self.problem, self.ws_ptr, self.ws_bytes, dL.data_ptr(), self._grad_structs,
+                                     self.stream()), "ubs_render_bwd")
+        return self.grads
+
+    def render_bwd_blend(self, dL_dimage: torch.Tensor):
+        self._check(U.ubs_render_bwd_blend(self.problem, self.ws_ptr, self.ws_bytes, dL_dimage.data_ptr(),
+                                           self.stream()), "ubs_render_bwd_blend")
+
+    def render_bwd_params(self):
+        self._check(U.ubs_render_bwd_params(self.problem, self.ws_ptr, self.ws_bytes, self._grad_structs,
+                                            self.stream()), "ubs_render_bwd_params")
+        return self.grads
+
+    def forward(self, check: bool = True, image=None):
+        """Full forward.  With ``check`` the call synchronises once to read the
+        device status and, if the instance capacity was too small, grows it
+        and runs preprocess/bin_sort again."""
+        self.preprocess()
+        self.bin_sort()
+        if check:
+            st = self.status()
+            if st.status == U.UBS_ERR_CAPACITY:
+                self.set_capacity(int(st.instances * 1.25) + 1024)
+                self.preprocess()
+                self.bin_sort()
+                st = self.status()
+            if st.status != U.UBS_OK:
+                raise U.UBSError(st.status, "device status")
+        return self.render_fwd(image)
+
+    def backward(self, dL_dimage):
+        return self.render_bwd(dL_dimage)
+
+    # -- helpers
+    def view_image(self, flat: torch.Tensor, v: int) -> torch.Tensor:
+        w = self.views[v]
+        o = int(self.pix_off[v]) * 3
+        return flat[o:o + 3 * w.height * w.width].view(3, w.height, w.width)
+
+    def pack(self, images) -> torch.Tensor:
+        return torch.cat([torch.as_tensor(im, dtype=torch.float32).reshape(-1) for im in images]).to(self.device)
+
+    def export(self, what: int, dtype=torch.int32, count=None):
+        st, need = U.ubs_export(self.problem, self.ws_ptr, self.ws_bytes, what, None, 0, self.stream())
+        self._check(st, "ubs_export")
+        out = torch.empty(need, dtype=torch.uint8, device=self.device)
+        st, _ = U.ubs_export(self.problem, self.ws_ptr, self.ws_bytes, what, out.data_ptr(), need, self.stream())
+        self._check(st, "ubs_export")
+        return out.view(dtype)
+
+
+class UBSRasterize(torch.autograd.Function):
+    """Differentiable rendering of one problem.  ``params`` are the scenes'
+    [K, P] tensors the rasterizer was built on; the output is the packed
+    images.  The backward is the hand-written CUDA backward (render_bwd)."""
+
+    @staticmethod
+    def forward(ctx, rasterizer: Rasterizer, *params):
+        for p, s in zip(params, rasterizer.scenes):
+            if p.data_ptr() != s.params.data_ptr():
+                raise ValueError("params must be the tensors the rasterizer was built on")
+        ctx.rasterizer = rasterizer
+        return rasterizer.forward(image=torch.empty_like(rasterizer.image))
+
+    @staticmethod
+    def backward(ctx, dimg):
+        grads = ctx.rasterizer.backward(dimg.contiguous())
+        return (None, *[g.clone() for g in grads])
+
+
+def rasterize(rasterizer: Rasterizer, *params):
+    return UBSRasterize.apply(rasterizer, *params)

@@ -1,0 +1,141 @@
+"""Helpers of the GPU parity tests: run the CUDA path through the C-ABI and
+compare it with the oracle on the same seeded inputs."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from oracle import binning, fp32_spec
+from oracle import render64 as R64
+from paper_2510_03312_gb300 import raster
+from paper_2510_03312_gb300 import ubs as U
+
+IMG_TOL = 1e-4   # maximum absolute image error (float32 image vs float64 oracle)
+GRAD_TOL = 1e-3  # per-parameter-group relative gradient error
+
+
+def gpu_forward(scenes, views, cfg, capacity=None):
+    dev = [raster.DeviceScene.from_scene(s) for s in scenes]
+    r = raster.Rasterizer(dev, views, cfg, capacity=capacity)
+    img = r.forward(check=True)
+    st = r.status()
+    torch.cuda.synchronize()
+    out = {"rast": r, "dev": dev, "status": st, "image_flat": img}
+    out["images"] = [r.view_image(img, v).cpu().numpy() for v in range(len(views))]
+    out["tiles"] = r.export(U.EXPORT_TILES).cpu().numpy().view(np.uint32)
+    out["keys"] = r.export(U.EXPORT_KEYS).cpu().numpy().view(np.uint32)
+    out["rect"] = r.export(U.EXPORT_RECT).cpu().numpy().view(np.uint32).reshape(-1, 2)
+    out["rec"] = r.export(U.EXPORT_RECORDS, torch.float32).cpu().numpy().reshape(-1, 12)
+    n = int(st.instances)
+    out["instances"] = r.export(U.EXPORT_INSTANCES).cpu().numpy().view(np.uint32)[:n]
+    out["tstart"] = r.export(U.EXPORT_TILE_START).cpu().numpy().view(np.uint32)
+    out["T"] = r.export(U.EXPORT_FINAL_T, torch.float32).cpu().numpy()
+    out["last"] = r.export(U.EXPORT_LAST).cpu().numpy().view(np.uint32)
+    return out
+
+
+def check_preprocess(gpu, orc):
+    """Bit-exact integer outputs and float32 values; double-float screen mean
+    against float64."""
+    recs = orc.records(orc.leaves())
+    for vi, (pre, rec64) in enumerate(zip(orc.pre32, recs)):
+        o = int(orc.rec_off[vi])
+        P = pre["valid"].size
+        tiles = gpu["tiles"][o:o + P].astype(np.int64)
+        assert np.array_equal(tiles, pre["tiles_touched"]), f"view {vi}: tiles_touched differ"
+        v = pre["valid"]
+        assert np.array_equal(tiles > 0, v)
+        assert np.array_equal(gpu["keys"][o:o + P][v], pre["depth_bits"][v]), f"view {vi}: depth keys differ"
+        rc = gpu["rect"][o:o + P][v]
+        rect = np.stack([rc[:, 0] & 0xFFFF, rc[:, 0] >> 16, rc[:, 1] & 0xFFFF, rc[:, 1] >> 16]).astype(np.int64)
+        assert np.array_equal(rect, pre["rect"][:, v]), f"view {vi}: rectangles differ"
+        g = gpu["rec"][o:o + P][v]
+        assert np.array_equal(g[:, 4:7].view(np.uint32), pre["conic"].T[v].view(np.uint32)), "conic bits"
+        assert np.array_equal(g[:, 8].view(np.uint32), pre["beta_x"][v].view(np.uint32)), "beta bits"
+        oq = np.exp2(g[:, 7].astype(np.float64))
+        np.testing.assert_allclose(oq, pre["opacity"][v], rtol=2e-6)
+        mu = g[:, 0:2].astype(np.float64) + g[:, 2:4].astype(np.float64)
+        mu64 = rec64["mean2d"].detach().numpy()[v]
+        tol = 1e-6 if orc.scenes[orc.views[vi].scene_id].N == 3 else 2e-4
+        assert np.abs(mu - mu64).max() <= tol, np.abs(mu - mu64).max()
+    return recs
+
+
+def check_bins(gpu, orc):
+    b = orc.bins
+    n = b["record"].size
+    assert int(gpu["status"].instances) == n, (int(gpu["status"].instances), n)
+    assert np.array_equal(gpu["instances"].astype(np.int64), b["record"]), "sorted instance lists differ"
+    starts = gpu["tstart"].astype(np.int64)
+    assert np.array_equal(starts[:-1], b["ranges"][:, 0]) and np.array_equal(starts[1:], b["ranges"][:, 1])
+
+
+def check_images(gpu, orc, recs=None, tiles=None, tol=IMG_TOL):
+    """Every pixel within tol of the float64 value, or of one admissible
+    result where the oracle flagged a near-threshold decision.  Returns
+    (max error on unflagged pixels, flagged pixel count)."""
+    ref = orc.render(tiles=tiles, recs=recs)
+    worst, nflag = 0.0, 0
+    for vi in range(len(orc.views)):
+        a = gpu["images"][vi].astype(np.float64)
+        r = ref["image"][vi].detach().numpy()
+        m = ~np.isnan(r[0])
+        flag = ref["flag"][vi].numpy() & m
+        nflag += int(flag.sum())
+        err = np.abs(a - r).max(0)
+        ok = m & ~flag
+        if ok.any():
+            worst = max(worst, float(err[ok].max()))
+        bad = np.argwhere(ok & (err > tol))
+        assert bad.size == 0, f"view {vi}: {len(bad)} unflagged pixels off by up to {err[ok].max():.3e}"
+        off = m & flag & (err > tol)
+        for y, x in np.argwhere(off):
+            alts = orc.admissible(vi, int(x), int(y), recs=recs)
+            d = min(np.abs(np.asarray(c) - a[:, y, x]).max() for c, _, _ in alts)
+            assert d <= tol, f"view {vi} pixel ({x},{y}): {d:.3e} from every admissible value"
+        # transmittance and last contributor on unflagged pixels
+        T = gpu["T"][orc_pix(orc, vi)].reshape(r.shape[1:])
+        assert np.abs(T - ref["T"][vi].numpy())[ok].max() <= tol
+        last = gpu["last"][orc_pix(orc, vi)].reshape(r.shape[1:]).astype(np.int64)
+        assert np.array_equal(last[ok], ref["last"][vi].numpy()[ok])
+    return worst, nflag, ref
+
+
+def orc_pix(orc, vi):
+    off = sum(v.width * v.height for v in orc.views[:vi])
+    v = orc.views[vi]
+    return slice(off, off + v.width * v.height)
+
+
+def check_grads(gpu, orc, ref_render, seed=7, tiles=None, tol=GRAD_TOL):
+    """GPU backward against the oracle's autograd gradient for the same
+    dL/dimage (zero on flagged pixels and outside the rendered tiles)."""
+    rng = np.random.default_rng(seed)
+    gl = []
+    for vi, v in enumerate(orc.views):
+        g = rng.standard_normal((3, v.height, v.width)).astype(np.float32) / (v.height * v.width)
+        fl = ref_render["flag"][vi].numpy() | np.isnan(ref_render["image"][vi].detach().numpy()[0])
+        g[:, fl] = 0.0
+        gl.append(g)
+    out = R64.loss_grads(orc, [x.astype(np.float64) for x in gl], tiles=tiles)
+    r = gpu["rast"]
+    grads = r.backward(r.pack(gl))
+    torch.cuda.synchronize()
+    worst = {}
+    for si, sc in enumerate(orc.scenes):
+        ga = grads[si].cpu().numpy()
+        for name, (o, n) in sc.offsets().items():
+            if n == 0:
+                continue
+            a = ga[o:o + n].astype(np.float64)
+            ref = out["params"][si][name]
+            scale = np.abs(ref).max()
+            if scale == 0:
+                assert np.abs(a).max() == 0, name
+                continue
+            e = np.abs(a - ref).max() / scale
+            worst[f"{si}:{name}"] = e
+            assert e <= tol, f"scene {si} {name}: relative error {e:.2e}"
+    return worst

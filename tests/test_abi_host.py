@@ -1,0 +1,106 @@
+"""The C-ABI library loads on the host, exports every entry point that
+include/ubs.h declares, and validates arguments without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2510_03312_gb300 import build as B
+from paper_2510_03312_gb300 import scenes as S
+from paper_2510_03312_gb300 import ubs as U
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return U.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "ubs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ubs_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_path_entry_points():
+    names = _declared()
+    for n in ("ubs_preprocess", "ubs_bin_sort", "ubs_render_fwd", "ubs_render_bwd"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in U.SIGNATURES, n
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert U.ubs_status_string(code)
+    assert U.ubs_status_string(0) == "ok"
+
+
+def _problem(scene_N=3, P=100, tile=(16, 16), views=1, cap=1000):
+    sc = U.ubs_scene()
+    sc.N, sc.rot_mode, sc.P = scene_N, 0, P
+    fake = 0x10000  # never dereferenced by host-side validation
+    for name in S.PLANE_ORDER:
+        setattr(sc, name, fake)
+    scs = (U.ubs_scene * 1)(sc)
+    vs = (U.ubs_view * views)()
+    for i in range(views):
+        vs[i].fx = vs[i].fy = 100.0
+        vs[i].width, vs[i].height = 130, 70
+    pr = U.ubs_problem()
+    pr.scenes, pr.n_scenes, pr.views, pr.n_views = scs, 1, vs, views
+    pr.cfg.tile_w, pr.cfg.tile_h = tile
+    pr.cfg.alpha_min, pr.cfg.alpha_max, pr.cfg.T_min = 1 / 255, 0.99, 1e-4
+    pr.cfg.eps2d, pr.cfg.near_plane, pr.cfg.jac_clip = 0.3, 0.2, 1.3
+    pr.instance_capacity = cap
+    return pr, (scs, vs)
+
+
+def test_workspace_size_is_host_arithmetic(lib):
+    pr, keep = _problem()
+    n1 = U.ubs_workspace_size(pr)
+    assert n1 > 0 and n1 % 256 == 0
+    pr.instance_capacity = 100000
+    assert U.ubs_workspace_size(pr) > n1
+    pr2, keep2 = _problem(views=3)
+    assert U.ubs_workspace_size(pr2) > n1
+
+
+@pytest.mark.parametrize("bad", ["N", "tile", "views", "cap", "scene_id", "size"])
+def test_invalid_problems_are_rejected(lib, bad):
+    pr, keep = _problem()
+    if bad == "N":
+        keep[0][0].N = 5
+    elif bad == "tile":
+        pr.cfg.tile_w = 12
+    elif bad == "views":
+        pr.n_views = 0
+    elif bad == "cap":
+        pr.instance_capacity = -1
+    elif bad == "scene_id":
+        keep[1][0].scene_id = 3
+    elif bad == "size":
+        keep[1][0].width = 0
+    assert U.ubs_workspace_size(pr) == 0
+    # the entry points reject it synchronously, before any CUDA call
+    assert U.ubs_preprocess(pr, 0x100000, 1 << 30, None) == U.UBS_ERR_INVALID_ARG
+
+
+def test_workspace_checks(lib):
+    pr, keep = _problem()
+    need = U.ubs_workspace_size(pr)
+    assert U.ubs_preprocess(pr, None, need, None) == U.UBS_ERR_INVALID_ARG
+    assert U.ubs_preprocess(pr, 0x100010, need, None) == U.UBS_ERR_ALIGNMENT
+    assert U.ubs_bin_sort(pr, 0x100000, need - 256, None) == U.UBS_ERR_WORKSPACE
+    keep[0][0].mean_x = 0x10002
+    assert U.ubs_preprocess(pr, 0x100000, need, None) == U.UBS_ERR_ALIGNMENT

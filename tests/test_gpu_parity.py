@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Bit-exact: culling, depth keys, tile rectangles, float32 conic/beta, sorted
+instance lists and tile ranges.  Images: maximum absolute error 1e-4 against
+float64 (admissible branches near thresholds).  Gradients: relative error
+1e-3 per parameter group against the oracle's autograd gradients.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import render64 as R64
+from paper_2510_03312_gb300 import scenes as S
+
+from parity_tools import check_bins, check_grads, check_images, check_preprocess, gpu_forward
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_03312_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _multi(N, P, nv, W, H, seed, mode=S.ROT_QUAT, tile=(16, 16), extent=2.0, radius=5.0):
+    rng = np.random.default_rng(seed)
+    sc = S.make_scene(seed, N, P, means="clusters", extent=extent, n_clusters=8, rot_mode=mode, rng=rng)
+    views = S.sphere_views(rng, nv, radius, W, H, hemisphere=True, times=list(rng.uniform(0, 1, nv)))
+    cfg = S.RasterConfig(tile_w=tile[0], tile_h=tile[1])
+    return [sc], views, cfg
+
+
+CASES = {
+    "static_small": lambda: (lambda w: (w.scenes, w.views, w.cfg))(S.workload_static_small()),
+    "n3_ragged_2views": lambda: _multi(3, 3000, 2, 200, 150, 11),
+    "n3_skew": lambda: _multi(3, 2500, 1, 160, 120, 12, mode=S.ROT_SKEW1),
+    "n6_3views": lambda: _multi(6, 12000, 3, 176, 132, 13),
+    "n7_3views": lambda: _multi(7, 30000, 3, 150, 110, 14),
+    "n4_2views": lambda: _multi(4, 6000, 2, 130, 90, 15),
+    "tile8": lambda: _multi(3, 3000, 1, 120, 100, 16, tile=(8, 8)),
+    "tile16x32": lambda: _multi(3, 3000, 1, 120, 100, 17, tile=(16, 32)),
+    "tile32": lambda: _multi(3, 3000, 1, 140, 100, 18, tile=(32, 32)),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_forward_parity(case):
+    scenes, views, cfg = CASES[case]()
+    orc = R64.Oracle(scenes, views, cfg)
+    gpu = gpu_forward(scenes, views, cfg)
+    assert gpu["status"].status == 0
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    worst, nflag, _ = check_images(gpu, orc, recs=recs)
+    print(f"{case}: max image error {worst:.2e}, flagged pixels {nflag}")
+
+
+@pytest.mark.parametrize("case", ["n3_ragged_2views", "n3_skew", "n6_3views", "n7_3views", "n4_2views",
+                                  "tile8", "tile32"])
+def test_backward_parity(case):
+    scenes, views, cfg = CASES[case]()
+    orc = R64.Oracle(scenes, views, cfg)
+    gpu = gpu_forward(scenes, views, cfg)
+    recs = orc.records(orc.leaves())
+    _, _, ref = check_images(gpu, orc, recs=recs)
+    worst = check_grads(gpu, orc, ref)
+    print(case, {k: f"{v:.1e}" for k, v in worst.items()})
+
+
+def test_uneven_batch_of_scenes():
+    """Several scenes of different N, views of different sizes, one problem."""
+    scenes = [S.make_scene(40, 3, 2000, means="clusters", extent=2.0, n_clusters=6),
+              S.make_scene(41, 6, 8000, means="clusters", extent=2.0, n_clusters=6),
+              S.make_scene(42, 7, 20000, means="clusters", extent=2.0, n_clusters=6)]
+    rng = np.random.default_rng(43)
+    views = []
+    for k, (W, H) in enumerate([(96, 64), (130, 77), (64, 140), (100, 100), (33, 47)]):
+        R, t = S.look_at(5.0 * (lambda u: u / np.linalg.norm(u))(rng.standard_normal(3)))
+        views.append(S.make_view(R, t, W, H, time=float(rng.uniform()), scene_id=k % 3))
+    cfg = S.RasterConfig()
+    orc = R64.Oracle(scenes, views, cfg)
+    gpu = gpu_forward(scenes, views, cfg)
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    _, _, ref = check_images(gpu, orc, recs=recs)
+    check_grads(gpu, orc, ref)
+
+
+def test_everything_culled_renders_background():
+    sc = S.make_scene(50, 3, 500, means="uniform", extent=1.0)
+    R, t = S.look_at((0.0, 0.0, -3.0), target=(0.0, 0.0, -10.0))
+    v = S.make_view(R, t, 64, 48)
+    cfg = S.RasterConfig(bg=(0.25, 0.5, 0.75))
+    gpu = gpu_forward([sc], [v], cfg)
+    assert gpu["status"].visible_records == 0 and gpu["status"].instances == 0
+    img = gpu["images"][0]
+    for c, b in enumerate(cfg.bg):
+        assert np.all(img[c] == np.float32(b))
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    scenes, views, cfg = CASES["n3_ragged_2views"]()
+    orc = R64.Oracle(scenes, views, cfg)
+    need = orc.bins["record"].size
+    gpu = gpu_forward(scenes, views, cfg, capacity=need // 3)
+    # forward(check=True) grew the capacity and re-ran
+    assert gpu["rast"].capacity >= need
+    check_bins(gpu, orc)
+    r = gpu["rast"]
+    r.set_capacity(need // 3)
+    r.problem.instance_capacity = need // 3
+    r.preprocess()
+    r.bin_sort()
+    st = r.status()
+    assert st.status == 3 and st.instances == need  # UBS_ERR_CAPACITY with the required count
+
+
+def test_tiny_and_single_pixel_views():
+    sc = S.make_scene(60, 3, 400, means="uniform", extent=0.5, scale_range=(0.05, 0.3))
+    R, t = S.look_at((0.0, 0.0, -2.5))
+    views = [S.make_view(R, t, 1, 1), S.make_view(R, t, 17, 3), S.make_view(R, t, 3, 33)]
+    cfg = S.RasterConfig()
+    orc = R64.Oracle([sc], views, cfg)
+    gpu = gpu_forward([sc], views, cfg)
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    check_images(gpu, orc, recs=recs)
+
+
+def test_large_screen_filling_primitive():
+    sc = S.make_scene(61, 3, 8, means="uniform", extent=0.1, scale_range=(0.5, 1.5))
+    R, t = S.look_at((0.0, 0.0, -2.0))
+    v = S.make_view(R, t, 300, 200)
+    cfg = S.RasterConfig()
+    orc = R64.Oracle([sc], [v], cfg)
+    gpu = gpu_forward([sc], [v], cfg)
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    _, _, ref = check_images(gpu, orc, recs=recs)
+    check_grads(gpu, orc, ref)
+
+
+def test_full_size_static_sampled():
+    """The 1M-primitive 1600x1060 workload in the launch configuration the
+    benchmark times: all records and instance lists bit-exact, images and
+    gradients on sampled tiles."""
+    wl = S.workload_static_large()
+    orc = R64.Oracle(wl.scenes, wl.views, wl.cfg)
+    gpu = gpu_forward(wl.scenes, wl.views, wl.cfg)
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    counts = np.diff(orc.bins["ranges"], axis=1)[:, 0]
+    order = np.argsort(-counts)
+    rng = np.random.default_rng(0)
+    tiles = sorted(set(order[:4].tolist()) | set(rng.choice(counts.size, 8, replace=False).tolist()))
+    worst, nflag, ref = check_images(gpu, orc, recs=recs, tiles=tiles)
+    print(f"full size: max image error {worst:.2e} on {len(tiles)} tiles, flagged {nflag}")
+    check_grads(gpu, orc, ref, tiles=tiles)
