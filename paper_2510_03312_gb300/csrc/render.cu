@@ -1,26 +1,35 @@
 // render.cu -- R1 (forward blend) and G1 (backward blend).
 //
-// One CTA per screen tile, one thread per pixel.  The tile's front-to-back
-// list (sorted record ids) is consumed in batches of one record per thread:
-// each batch's 48-byte render records are staged in shared memory, then every
-// thread walks the batch.  Per pair (Sec. 3, Eq. r; Sec. 4.3 final density):
-//   dx = (px - hi_x) - lo_x,  r = a dx^2 + 2 b dx dy + c dy^2,
+// One CTA per screen tile, one thread per pixel; each warp owns an 8x4 pixel
+// block of the tile.  The tile's front-to-back list (sorted record ids) is
+// consumed in batches of up to 256 records: each batch's 48-byte render
+// records are staged in shared memory together with a conservative screen
+// box of each record's support (the ellipse r <= r_cut, r_cut the radius
+// beyond which alpha < alpha_min, widened by a margin).  A warp skips a
+// record whose box misses its block -- a warp-uniform branch that can only
+// drop pairs whose alpha is below alpha_min, so no decision changes.
+//
+// Per pair (Sec. 3, Eq. r; Sec. 4.3 final density), with the screen mean
+// staged relative to the tile origin o as m = (hi - o) + lo:
+//   dx = (px - o) - m,  r = a dx^2 + 2 b dx dy + c dy^2,
 //   skip if r >= 1;  alpha = min(alpha_max, 2^(beta_x log2(1 - r) + log2 o(q)))
 //   skip if alpha < alpha_min;  stop before T (1 - alpha) < T_min;
 //   C += c alpha T;  T *= 1 - alpha.
 // log2/exp2 are the MUFU approximations (lg2.approx, ex2.approx).  The pair
 // evaluation is one inline function with explicit rounding so that the
 // backward kernel re-derives exactly the forward's alpha and decisions.
-// A CTA stops loading batches once every pixel of the tile has terminated
-// (__syncthreads_count).
+// A CTA stops loading batches once every pixel of the tile has terminated.
+//
+// Each warp first lists the batch entries whose box meets its block (32 boxes
+// per ballot), then walks only that list, two entries at a time.
 //
 // The backward walks each tile's list back to front from the last
-// contributor, recovers T by division, and forms per-pair gradients of
-// (mu', conic, log2 o(q), beta_x, rgb).  They are summed over the warp's 32
-// pixels with shuffles (only for records some lane of the warp touches),
-// accumulated per record in shared memory across the CTA's warps, and
-// flushed with one vector atomic add per (record, tile) -- never one global
-// atomic per pixel.
+// contributor, recovers T by division and forms per-pair gradients of
+// (mu', conic, log2 o(q), beta_x, rgb).  They are summed over the warp's
+// lanes with a transposed butterfly (reduce-scatter: 12 shuffles for the 10
+// values, leaving each total in one lane), added per record in shared memory
+// across the CTA's warps, and flushed with one vector atomic add per
+// (record, tile) -- never one global atomic per pixel.
 #include "kernels.cuh"
 
 namespace ubs {
@@ -40,21 +49,55 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-struct PairEval {
-  float dx, dy, r, lg, alpha;
+// A staged record, tile-relative: the screen mean is re-expressed relative to
+// the tile origin (hi - origin) + lo, exact for the subtraction and rounded
+// once, so that per pair dx = (pixel centre - origin) - mean costs one add.
+struct Staged {
+  float4 p;   // mean_x, mean_y (tile-relative), a, 2b
+  float4 q;   // c, log2 o(q), beta_x, red
+  float2 s;   // green, blue
 };
 
-// the one definition of a pair's alpha, shared by forward and backward
-__device__ __forceinline__ void eval_pair(float px, float py, const float4& a, const float4& c, float beta,
+__device__ __forceinline__ void stage_record(const float4* __restrict__ rec4, uint32_t r, float ox, float oy,
+                                             float lg2_amin, Staged& st, float4& box) {
+  const float4 a = rec4[3 * (size_t)r], c = rec4[3 * (size_t)r + 1], d = rec4[3 * (size_t)r + 2];
+  st.p = make_float4(__fadd_rn(__fsub_rn(a.x, ox), a.z), __fadd_rn(__fsub_rn(a.y, oy), a.w), c.x,
+                     __fmul_rn(2.0f, c.y));
+  st.q = make_float4(c.z, c.w, d.x, d.y);
+  st.s = make_float2(d.z, d.w);
+  // conservative box of the pixels with alpha >= alpha_min: the ellipse
+  // r <= r_cut, r_cut = 1 - (alpha_min/o(q))^(1/beta_x), widened by 2% + 0.02
+  // in r_cut and 0.1 px; empty when o(q) < alpha_min
+  const float det = c.x * c.z - c.y * c.y;
+  const float s00 = c.z / det, s11 = c.x / det;
+  float rc = 1.0f - ex2_approx((lg2_amin - c.w) / d.x);
+  if (!(rc > -0.02f)) {
+    box = make_float4(1.0f, -1.0f, 1.0f, -1.0f);
+  } else {
+    rc = fminf(1.0f, fmaf(rc, 1.02f, 0.02f));
+    const float ex = sqrtf(fmaxf(rc * s00, 0.0f)) + 0.1f, ey = sqrtf(fmaxf(rc * s11, 0.0f)) + 0.1f;
+    box = make_float4(st.p.x - ex, st.p.x + ex, st.p.y - ey, st.p.y + ey);
+  }
+}
+
+struct PairEval {
+  float dx, dy, r, om, lg, alpha;
+  bool use;
+};
+
+// the one definition of a pair's alpha and skip decision, shared by the
+// forward and backward kernels: (lx, ly) is the pixel centre relative to the
+// tile origin
+__device__ __forceinline__ void eval_pair(float lx, float ly, const float4& p, const float4& q, float amin,
                                           float amax, PairEval& e) {
-  e.dx = __fsub_rn(__fsub_rn(px, a.x), a.z);
-  e.dy = __fsub_rn(__fsub_rn(py, a.y), a.w);
-  const float t0 = __fmul_rn(c.x, e.dx);
-  const float t1 = __fmul_rn(c.z, e.dy);
-  const float bxy = __fmul_rn(__fmul_rn(2.0f, c.y), e.dy);
-  e.r = __fmaf_rn(t0, e.dx, __fmaf_rn(t1, e.dy, __fmul_rn(bxy, e.dx)));
-  e.lg = lg2_approx(__fsub_rn(1.0f, e.r));
-  e.alpha = fminf(amax, ex2_approx(__fmaf_rn(beta, e.lg, c.w)));
+  e.dx = __fsub_rn(lx, p.x);
+  e.dy = __fsub_rn(ly, p.y);
+  const float t = __fmaf_rn(p.z, e.dx, __fmul_rn(p.w, e.dy));
+  e.r = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(q.x, e.dy), e.dy));
+  e.om = __fsub_rn(1.0f, e.r);
+  e.lg = lg2_approx(fmaxf(e.om, 0.0f));
+  e.alpha = fminf(amax, ex2_approx(__fmaf_rn(q.z, e.lg, q.y)));
+  e.use = (e.r < 1.0f) && (e.alpha >= amin);
 }
 
 __device__ __forceinline__ int find_view(const ViewDev* __restrict__ views, int V, uint32_t g) {
@@ -66,17 +109,51 @@ __device__ __forceinline__ int find_view(const ViewDev* __restrict__ views, int 
   return lo;
 }
 
+// pixel of this thread: warps tile the TWxTH tile with 8x4 blocks
+template <int TW>
+__device__ __forceinline__ void pixel_of(int& lx, int& ly, int& bx, int& by) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int WPR = TW / 8;  // warps per row of blocks
+  bx = (w % WPR) * 8;
+  by = (w / WPR) * 4;
+  lx = bx + (lane & 7);
+  ly = by + (lane >> 3);
+}
+
+__device__ __forceinline__ bool box_hits(const float4& bb, float x0, float x1, float y0, float y1) {
+  return bb.x <= x1 && bb.y >= x0 && bb.z <= y1 && bb.w >= y0;
+}
+
+// Each warp lists, in order, the staged entries j < n whose box meets its
+// block (all of them when `all`); returns the count.
+__device__ __forceinline__ int warp_cull_list(const float4* s_bb, int n, bool all, float x0, float x1, float y0,
+                                              float y1, uint8_t* list) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int cnt = 0;
+  for (int k = 0; k < n; k += 32) {
+    const int j = k + lane;
+    const bool hit = j < n && (all || box_hits(s_bb[j], x0, x1, y0, y1));
+    const unsigned m = __ballot_sync(kFull, hit);
+    if (hit) list[cnt + __popc(m & lt)] = (uint8_t)j;
+    cnt += __popc(m);
+  }
+  __syncwarp();
+  return cnt;
+}
+
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(TW * TH) render_fwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg,
-                                                             const uint32_t* __restrict__ tstart,
-                                                             const uint32_t* __restrict__ ivals,
-                                                             const float4* __restrict__ rec4,
-                                                             float* __restrict__ image, float* __restrict__ Tfin,
-                                                             uint32_t* __restrict__ lastc, const Header* hdr,
-                                                             uint32_t R, uint32_t* __restrict__ pairs) {
+__global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 8))
+    render_fwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
+                      const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
+                      float* __restrict__ image, float* __restrict__ Tfin, uint32_t* __restrict__ lastc,
+                      const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs) {
   constexpr int B = TW * TH;
   constexpr int BS = B < 256 ? B : 256;  // records staged per batch
-  __shared__ float4 s_a[BS], s_c[BS], s_d[BS];
+  constexpr int NW = B / 32;
+  __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
+  __shared__ float2 s_s[BS];
+  __shared__ uint8_t s_list[NW][BS];
   __shared__ int s_v;
   if (hdr->status != 0) return;
   const uint32_t g = blockIdx.x;
@@ -85,9 +162,15 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(const ViewDev* __re
   const ViewDev& v = views[s_v];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
-  const int x = tx * TW + (threadIdx.x % TW), y = ty * TH + (threadIdx.x / TW);
+  int lx, ly, bx, by;
+  pixel_of<TW>(lx, ly, bx, by);
+  const int x = tx * TW + lx, y = ty * TH + ly;
   const bool inside = x < v.W && y < v.H;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const float ox = (float)(tx * TW), oy = (float)(ty * TH);
+  const float fx = (float)lx + 0.5f, fy = (float)ly + 0.5f;  // pixel centre, tile-relative
+  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 3.0f;
+  const float lg2_amin = lg2_approx(cfg.amin);
+  uint8_t* list = s_list[threadIdx.x >> 5];
   const uint32_t start = tstart[g], end = tstart[g + 1];
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
   uint32_t last = 0, np = 0;
@@ -96,31 +179,60 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(const ViewDev* __re
     if (__syncthreads_count(done) == B) break;
     const uint32_t idx = base + threadIdx.x;
     if (threadIdx.x < BS && idx < end) {
-      const uint32_t r = min(ivals[idx], R - 1);  // ids are < R by construction
-      s_a[threadIdx.x] = rec4[3 * (size_t)r];
-      s_c[threadIdx.x] = rec4[3 * (size_t)r + 1];
-      s_d[threadIdx.x] = rec4[3 * (size_t)r + 2];
+      Staged st;
+      float4 box;
+      stage_record(rec4, min(ivals[idx], R - 1), ox, oy, lg2_amin, st, box);  // ids are < R by construction
+      s_p[threadIdx.x] = st.p;
+      s_q[threadIdx.x] = st.q;
+      s_s[threadIdx.x] = st.s;
+      s_bb[threadIdx.x] = box;
     }
     __syncthreads();
     const int n = (int)min((uint32_t)BS, end - base);
-    for (int j = 0; j < n && !done; ++j) {
-      const float4 a = s_a[j], c = s_c[j], d = s_d[j];
-      PairEval e;
-      eval_pair(px, py, a, c, d.x, cfg.amax, e);
-      if (!(e.r < 1.0f)) continue;
-      if constexpr (COUNT) ++np;
-      if (e.alpha < cfg.amin) continue;
-      const float Tn = T * (1.0f - e.alpha);
-      if (Tn < cfg.tmin) {
-        done = true;
-        break;
+    // the counting variant visits every pair with r < 1
+    const int cnt = warp_cull_list(s_bb, n, COUNT, wx0, wx1, wy0, wy1, list);
+    const uint32_t rel = base - start;
+    for (int i = 0; i < cnt; i += 2) {
+      if (__all_sync(kFull, done)) break;
+      // two entries evaluated independently, applied in order
+      const int j0 = list[i];
+      const bool has1 = i + 1 < cnt;
+      const int j1 = has1 ? list[i + 1] : j0;
+      PairEval e0, e1;
+      eval_pair(fx, fy, s_p[j0], s_q[j0], cfg.amin, cfg.amax, e0);
+      eval_pair(fx, fy, s_p[j1], s_q[j1], cfg.amin, cfg.amax, e1);
+      if constexpr (COUNT) np += (!done && e0.r < 1.0f);
+      if (!done && e0.use) {
+        const float Tn = T * (1.0f - e0.alpha);
+        if (Tn < cfg.tmin) {
+          done = true;
+        } else {
+          const float w = e0.alpha * T;
+          const float4 q = s_q[j0];
+          const float2 c2 = s_s[j0];
+          C0 = fmaf(q.w, w, C0);
+          C1 = fmaf(c2.x, w, C1);
+          C2 = fmaf(c2.y, w, C2);
+          T = Tn;
+          last = rel + j0 + 1;
+        }
       }
-      const float w = e.alpha * T;
-      C0 = fmaf(d.y, w, C0);
-      C1 = fmaf(d.z, w, C1);
-      C2 = fmaf(d.w, w, C2);
-      T = Tn;
-      last = base - start + j + 1;
+      if constexpr (COUNT) np += (!done && has1 && e1.r < 1.0f);
+      if (!done && has1 && e1.use) {
+        const float Tn = T * (1.0f - e1.alpha);
+        if (Tn < cfg.tmin) {
+          done = true;
+        } else {
+          const float w = e1.alpha * T;
+          const float4 q = s_q[j1];
+          const float2 c2 = s_s[j1];
+          C0 = fmaf(q.w, w, C0);
+          C1 = fmaf(c2.x, w, C1);
+          C2 = fmaf(c2.y, w, C2);
+          T = Tn;
+          last = rel + j1 + 1;
+        }
+      }
     }
   }
   if (inside) {
@@ -136,21 +248,75 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(const ViewDev* __re
   }
 }
 
+// Transposed-butterfly reduction of g[0..9] over the warp: each exchange
+// step halves the values a lane keeps, so 12 shuffles sum all 10.  On return
+// lane l holds the warp total of value writer_of(l) (when that is >= 0).
+__device__ __forceinline__ float warp_reduce10(const float (&g)[10], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  // bit 4: keep {0..4} (b4 = 0) or {5..9} (b4 = 1)
+  float p[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float keep = b4 ? g[i + 5] : g[i];
+    const float send = b4 ? g[i] : g[i + 5];
+    p[i] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+  // bit 3: slots (p0|p3, p1|p4, p2)
+  float s[3];
+  {
+    const float k0 = b3 ? p[3] : p[0], e0 = b3 ? p[0] : p[3];
+    const float k1 = b3 ? p[4] : p[1], e1 = b3 ? p[1] : p[4];
+    s[0] = k0 + __shfl_xor_sync(kFull, e0, 8);
+    s[1] = k1 + __shfl_xor_sync(kFull, e1, 8);
+    s[2] = p[2] + __shfl_xor_sync(kFull, p[2], 8);
+  }
+  // bit 2: slots (s0|s1, s2)
+  float t[2];
+  {
+    const float k0 = b2 ? s[1] : s[0], e0 = b2 ? s[0] : s[1];
+    t[0] = k0 + __shfl_xor_sync(kFull, e0, 4);
+    t[1] = s[2] + __shfl_xor_sync(kFull, s[2], 4);
+  }
+  // bit 1: slot t0|t1
+  const float k = b1 ? t[1] : t[0], e = b1 ? t[0] : t[1];
+  float u = k + __shfl_xor_sync(kFull, e, 2);
+  // bit 0
+  u += __shfl_xor_sync(kFull, u, 1);
+  return u;
+}
+
+// value index whose total `lane` holds after warp_reduce10, or -1 if the
+// lane is not that value's designated writer
+__device__ __forceinline__ int writer_of(int lane) {
+  if (lane & 1) return -1;
+  const int base = (lane & 16) ? 5 : 0;
+  if (lane & 2) return (lane & 12) ? -1 : base + 2;
+  return base + ((lane & 4) ? ((lane & 8) ? 4 : 1) : ((lane & 8) ? 3 : 0));
+}
+
+// Per-record sums accumulated by the backward blend (record constants a, b,
+// c, beta_x and ln 2 are applied once per record when flushing):
+//   v0 = sum q dx, v1 = sum q dy, v2 = sum q dx^2, v3 = sum q dx dy,
+//   v4 = sum q dy^2 with q = alpha dL/dalpha / (1 - r),
+//   v5 = sum alpha dL/dalpha, v6 = sum alpha dL/dalpha log2(1 - r),
+//   v7..9 = sum alpha T dL/dC.
+// With dr = -beta q:  d mu' = 2 beta [[a, b], [b, c]] (v0, v1),
+// d(a, b, c) = -beta (v2, 2 v3, v4), d log2 o = ln2 v5, d beta = ln2 v6.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) render_bwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg,
-                                                             const uint32_t* __restrict__ tstart,
-                                                             const uint32_t* __restrict__ ivals,
-                                                             const float4* __restrict__ rec4,
-                                                             const float* __restrict__ dLdimg,
-                                                             const float* __restrict__ Tfin,
-                                                             const uint32_t* __restrict__ lastc,
-                                                             float4* __restrict__ g2d, const Header* hdr, uint32_t R) {
+__global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 8))
+    render_bwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
+                      const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
+                      const float* __restrict__ dLdimg, const float* __restrict__ Tfin,
+                      const uint32_t* __restrict__ lastc, float4* __restrict__ g2d, const Header* hdr, uint32_t R) {
   constexpr int B = TW * TH;
   constexpr int BS = B < 256 ? B : 256;  // records staged per batch
-  __shared__ float4 s_a[BS], s_c[BS], s_d[BS];
+  constexpr int NW = B / 32;
+  __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
+  __shared__ float2 s_s[BS];
   __shared__ uint32_t s_rec[BS];
   __shared__ float s_acc[10][BS];
   __shared__ int s_hit[BS];
+  __shared__ uint8_t s_list[NW][BS];
   __shared__ int s_v;
   __shared__ uint32_t s_max;
   if (hdr->status != 0) return;
@@ -165,10 +331,18 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(const ViewDev* __re
   const ViewDev& v = views[s_v];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
-  const int x = tx * TW + (threadIdx.x % TW), y = ty * TH + (threadIdx.x / TW);
+  int lx, ly, bx, by;
+  pixel_of<TW>(lx, ly, bx, by);
+  const int x = tx * TW + lx, y = ty * TH + ly;
   const bool inside = x < v.W && y < v.H;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const float ox = (float)(tx * TW), oy = (float)(ty * TH);
+  const float fx = (float)lx + 0.5f, fy = (float)ly + 0.5f;
+  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 3.0f;
+  const float lg2_amin = lg2_approx(cfg.amin);
+  uint8_t* list = s_list[threadIdx.x >> 5];
   const uint32_t start = tstart[g];
+  const int lane = threadIdx.x & 31;
+  const int wslot = writer_of(lane);
   float T = 1.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f;
   uint32_t last = 0;
   if (inside) {
@@ -183,10 +357,10 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(const ViewDev* __re
   }
   // colour behind the current record, normalised by the transmittance after it
   float B0 = cfg.bg[0], B1 = cfg.bg[1], B2 = cfg.bg[2];
-  if (last) atomicMax(&s_max, last);
+  const uint32_t wlast = __reduce_max_sync(kFull, last);
+  if (lane == 0 && wlast) atomicMax(&s_max, wlast);
   __syncthreads();
   const uint32_t nmax = s_max;
-  const uint32_t lane = threadIdx.x & 31;
   // batches from the back: entries [lo, hi) with hi = nmax, nmax - BS, ...
   for (int hi = (int)nmax; hi > 0; hi -= BS) {
     const int lo = hi - BS > 0 ? hi - BS : 0;
@@ -194,74 +368,80 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(const ViewDev* __re
     __syncthreads();
     if ((int)threadIdx.x < n) {
       const uint32_t r = min(ivals[start + lo + threadIdx.x], R - 1);  // ids are < R by construction
+      Staged st;
+      float4 box;
+      stage_record(rec4, r, ox, oy, lg2_amin, st, box);
       s_rec[threadIdx.x] = r;
-      s_a[threadIdx.x] = rec4[3 * (size_t)r];
-      s_c[threadIdx.x] = rec4[3 * (size_t)r + 1];
-      s_d[threadIdx.x] = rec4[3 * (size_t)r + 2];
+      s_p[threadIdx.x] = st.p;
+      s_q[threadIdx.x] = st.q;
+      s_s[threadIdx.x] = st.s;
+      s_bb[threadIdx.x] = box;
     }
     __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-      const uint32_t entry = (uint32_t)(lo + j);
-      float g[10];
+    // entries past every lane's last contributor are not listed
+    const int nw = max(0, min(n, (int)wlast - lo));
+    const int cnt = warp_cull_list(s_bb, nw, false, wx0, wx1, wy0, wy1, list);
+    for (int i = cnt - 1; i >= 0; --i) {
+      const int j = list[i];
+      float gv[10];
       bool hit = false;
-      if (entry < last) {
-        const float4 a = s_a[j], c = s_c[j], d = s_d[j];
+      if ((uint32_t)(lo + j) < last) {
+        const float4 p = s_p[j], q = s_q[j];
         PairEval e;
-        eval_pair(px, py, a, c, d.x, cfg.amax, e);
-        if (e.r < 1.0f && e.alpha >= cfg.amin) {
+        eval_pair(fx, fy, p, q, cfg.amin, cfg.amax, e);
+        if (e.use) {
           hit = true;
-          const float om = 1.0f - e.alpha;
-          T = __fdividef(T, om);
+          const float2 c2 = s_s[j];
+          const float inv = __frcp_rn(e.om);  // 1 / (1 - r)
+          T = __fdividef(T, 1.0f - e.alpha);   // transmittance before this record
           const float w = e.alpha * T;
-          g[7] = w * G0;
-          g[8] = w * G1;
-          g[9] = w * G2;
-          const float dalpha = T * ((d.y - B0) * G0 + (d.z - B1) * G1 + (d.w - B2) * G2);
-          B0 = fmaf(e.alpha, d.y - B0, B0);
-          B1 = fmaf(e.alpha, d.z - B1, B1);
-          B2 = fmaf(e.alpha, d.w - B2, B2);
-          if (e.alpha < cfg.amax) {
-            const float ga = dalpha * e.alpha;
-            g[5] = ga * kLn2f;                       // d log2 o(q)
-            g[6] = ga * e.lg * kLn2f;                // d beta_x = alpha ln(1 - r)
-            const float dr = -ga * d.x / (1.0f - e.r);
-            g[0] = -2.0f * dr * (c.x * e.dx + c.y * e.dy);  // d mu'_x
-            g[1] = -2.0f * dr * (c.y * e.dx + c.z * e.dy);  // d mu'_y
-            g[2] = dr * e.dx * e.dx;
-            g[3] = 2.0f * dr * e.dx * e.dy;
-            g[4] = dr * e.dy * e.dy;
-          } else {
-#pragma unroll
-            for (int k = 0; k < 7; ++k) g[k] = 0.0f;
-          }
+          gv[7] = w * G0;
+          gv[8] = w * G1;
+          gv[9] = w * G2;
+          const float d0 = q.w - B0, d1 = c2.x - B1, d2 = c2.y - B2;
+          const float dalpha = T * fmaf(d0, G0, fmaf(d1, G1, d2 * G2));
+          B0 = fmaf(e.alpha, d0, B0);
+          B1 = fmaf(e.alpha, d1, B1);
+          B2 = fmaf(e.alpha, d2, B2);
+          const float ga = e.alpha < cfg.amax ? dalpha * e.alpha : 0.0f;
+          const float qq = ga * inv;
+          gv[0] = qq * e.dx;
+          gv[1] = qq * e.dy;
+          gv[2] = gv[0] * e.dx;
+          gv[3] = gv[0] * e.dy;
+          gv[4] = gv[1] * e.dy;
+          gv[5] = ga;
+          gv[6] = ga * e.lg;
         }
       }
+      const unsigned hits = __ballot_sync(kFull, hit);
+      if (hits == 0) continue;
       if (!hit) {
 #pragma unroll
-        for (int k = 0; k < 10; ++k) g[k] = 0.0f;
+        for (int k = 0; k < 10; ++k) gv[k] = 0.0f;
       }
-      const unsigned any = __ballot_sync(kFull, hit);
-      if (any) {
+      if (__popc(hits) == 1) {
+        if (hit) {
 #pragma unroll
-        for (int k = 0; k < 10; ++k) {
-          float s = g[k];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-          g[k] = s;
-        }
-        if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < 10; ++k) atomicAdd(&s_acc[k][j], g[k]);
+          for (int k = 0; k < 10; ++k) atomicAdd(&s_acc[k][j], gv[k]);
           s_hit[j] = 1;
         }
+      } else {
+        const float tot = warp_reduce10(gv, lane);
+        if (wslot >= 0) atomicAdd(&s_acc[wslot][j], tot);
+        if (lane == 0) s_hit[j] = 1;
       }
     }
     __syncthreads();
     if ((int)threadIdx.x < n && s_hit[threadIdx.x]) {
       const int j = threadIdx.x;
+      const float4 p = s_p[j], q = s_q[j];
+      const float a = p.z, b = 0.5f * p.w, c = q.x, beta = q.z;
+      const float v0 = s_acc[0][j], v1 = s_acc[1][j];
       float4* dst = g2d + 3 * (size_t)s_rec[j];
-      atomicAdd(dst, make_float4(s_acc[0][j], s_acc[1][j], s_acc[2][j], s_acc[3][j]));
-      atomicAdd(dst + 1, make_float4(s_acc[4][j], s_acc[5][j], s_acc[6][j], s_acc[7][j]));
+      atomicAdd(dst, make_float4(2.0f * beta * (a * v0 + b * v1), 2.0f * beta * (b * v0 + c * v1),
+                                 -beta * s_acc[2][j], -2.0f * beta * s_acc[3][j]));
+      atomicAdd(dst + 1, make_float4(-beta * s_acc[4][j], kLn2f * s_acc[5][j], kLn2f * s_acc[6][j], s_acc[7][j]));
       atomicAdd((float2*)(dst + 2), make_float2(s_acc[8][j], s_acc[9][j]));
 #pragma unroll
       for (int k = 0; k < 10; ++k) s_acc[k][j] = 0.0f;
