@@ -227,6 +227,29 @@ ubs_status ubs_export(const ubs_problem* problem, void* workspace, size_t worksp
 
 const char* ubs_status_string(ubs_status status);
 
+/* Forward rendering that allocates nothing.  (The paper has no counterpart:
+ * this serves callers that cannot allocate device memory when they render,
+ * such as plugin hosts without an allocator, processes confined to a
+ * pre-sized memory pool, or loops that forbid allocation after start-up.)
+ * Runs preprocess -> bin_sort -> render_fwd exactly like the entry points
+ * above, but takes the workspace from a fixed 32 MiB array in the library's
+ * own device memory instead of a caller-supplied buffer; the caller passes
+ * only the problem (device scene buffers as usual) and the output image.
+ * - Returns UBS_ERR_WORKSPACE, launching nothing, when
+ *   ubs_workspace_size(problem) exceeds 32 MiB.
+ * - Uses the array of the current device.  The first call on a device looks
+ *   up the array's device address with that device current; make that first
+ *   call before any stream capture.
+ * - Every call on a device shares the one array, which keeps the previous
+ *   call's contents (each step clears what must start at zero); calls whose
+ *   work overlaps on the GPU race on it.
+ * - As with ubs_bin_sort, if problem->instance_capacity is too small the
+ *   image is left unwritten; size the capacity for the scene.
+ * - Calls no cudaMalloc, cudaFree or allocating library routine.  The array
+ *   stays allocated on every GPU that loaded this part of the library until
+ *   the process exits. */
+ubs_status ubs_render_fwd_static(const ubs_problem* problem, float* image, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

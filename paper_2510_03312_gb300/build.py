@@ -28,6 +28,7 @@ UNITS = {
     "render.cu": [],
     "prim_backward.cu": [],
     "abi.cu": [],
+    "noalloc.cu": [],
 }
 
 

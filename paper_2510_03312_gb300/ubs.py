@@ -81,6 +81,7 @@ SIGNATURES = {
     "ubs_export": (c_int32, [POINTER(ubs_problem), c_void_p, c_size_t, c_int32, c_void_p, c_size_t,
                              POINTER(c_size_t), c_void_p]),
     "ubs_status_string": (c_char_p, [c_int32]),
+    "ubs_render_fwd_static": (c_int32, [POINTER(ubs_problem), c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -153,3 +154,7 @@ def ubs_export(problem, workspace, workspace_bytes, what, dst, dst_bytes, stream
 
 def ubs_status_string(status) -> str:
     return load().ubs_status_string(int(status)).decode()
+
+
+def ubs_render_fwd_static(problem, image, stream) -> int:
+    return int(load().ubs_render_fwd_static(ctypes.byref(problem), image, stream))
