@@ -3,7 +3,7 @@
 // host memory; ubs_read_status is the only one that synchronises.
 #include <string.h>
 
-#include "../../include/ubs.h"
+#include "ubs.h"
 #include "kernels.cuh"
 
 namespace ubs {
@@ -25,8 +25,6 @@ __global__ void upload_views_kernel(ViewChunk chunk, int n, ViewDev* dst) {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
-
-int plane_rows_rot(int rot_mode) { return rot_mode == UBS_ROT_QUAT ? 4 : 3; }
 
 ubs_status check_scene(const ubs_scene& s) {
   if (!(s.N == 3 || s.N == 4 || s.N == 6 || s.N == 7)) return UBS_ERR_INVALID_ARG;

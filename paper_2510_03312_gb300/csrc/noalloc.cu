@@ -20,7 +20,7 @@
 // streams, or different host threads) race on the array.
 #include <atomic>
 
-#include "../../include/ubs.h"
+#include "ubs.h"
 #include <cuda_runtime.h>
 
 namespace {

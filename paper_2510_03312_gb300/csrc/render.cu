@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
   __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
   __shared__ float2 s_s[BS];
   __shared__ uint32_t s_rec[BS];
-  __shared__ float s_acc[10][BS];
+  __shared__ float s_acc[10][BS + 1];  // +1: the 10 writer lanes hit 10 different banks
   __shared__ int s_hit[BS];
   __shared__ uint8_t s_list[NW][BS];
   __shared__ int s_v;
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     s_v = find_view(views, V, g);
     s_max = 0;
   }
-  for (int i = threadIdx.x; i < 10 * BS; i += B) (&s_acc[0][0])[i] = 0.0f;
+  for (int i = threadIdx.x; i < 10 * (BS + 1); i += B) (&s_acc[0][0])[i] = 0.0f;
   if (threadIdx.x < BS) s_hit[threadIdx.x] = 0;
   __syncthreads();
   const ViewDev& v = views[s_v];
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
 #pragma unroll
         for (int k = 0; k < 10; ++k) gv[k] = 0.0f;
       }
-      if (__popc(hits) == 1) {
+      if (__popc(hits) == 1) {  // one lane: its values are the totals
         if (hit) {
 #pragma unroll
           for (int k = 0; k < 10; ++k) atomicAdd(&s_acc[k][j], gv[k]);

@@ -46,6 +46,27 @@ __device__ __forceinline__ void st_rel32(uint32_t* p, uint32_t v) {
 
 __device__ __forceinline__ void set_status(Header* h, uint32_t s) { atomicCAS(&h->status, 0u, s); }
 
+#ifndef UBS_PEERS_BALLOT
+#define UBS_PEERS_BALLOT 1
+#endif
+
+// Lanes of the warp holding the same 9-bit value d (digits < 256, 0x100 for
+// "no item"): one ballot per bit, each lane keeping the lanes that agree.
+__device__ __forceinline__ uint32_t peer_mask(uint32_t d) {
+#if UBS_PEERS_BALLOT
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+#else
+  return __match_any_sync(0xffffffffu, d);
+#endif
+}
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
@@ -194,6 +215,7 @@ __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restri
 // ---------------------------------------------------------------- onesweep
 
 constexpr int kOsT = 256, kOsI = 16, kOsW = kOsT / 32, kOsTile = kOsT * kOsI;
+constexpr int kLbW = 1;  // look-back window (predecessor statuses loaded at once)
 
 // One stable pass of the LSD radix sort over 8 bits at `shift`.
 // ghist: global counts of this pass's digits over all n items.
@@ -227,7 +249,7 @@ __global__ void __launch_bounds__(kOsT) onesweep_kernel(const uint32_t* __restri
     k[i] = ok ? kin[idx] : 0u;
     v[i] = ok ? vin[idx] : 0u;
     const uint32_t d = ok ? (k[i] >> shift) & 255u : 0x100u;
-    const uint32_t peers = __match_any_sync(kFull, d);
+    const uint32_t peers = peer_mask(d);
     uint32_t cnt = 0;
     if (d < 256) cnt = s_hist[warp][d];
     __syncwarp();
@@ -245,7 +267,9 @@ __global__ void __launch_bounds__(kOsT) onesweep_kernel(const uint32_t* __restri
     s_hist[w][d] = acc;
     acc += c;
   }
-  // decoupled look-back for digit d
+  // decoupled look-back for digit d: the statuses of a window of kLbW
+  // predecessors are loaded together (independent loads in flight), then
+  // summed nearest-first up to the first inclusive prefix
   uint32_t excl = 0;
   uint32_t* st = stat + (size_t)tile * 256 + d;
   if (tile == 0) {
@@ -253,20 +277,28 @@ __global__ void __launch_bounds__(kOsT) onesweep_kernel(const uint32_t* __restri
   } else {
     st_rel32(st, kFlagAgg32 | acc);
     int64_t t = (int64_t)tile - 1;
-    while (t >= 0) {
-      uint32_t s = ld_acq32(stat + (size_t)t * 256 + d);
-      uint32_t spins = 0;
-      while ((s >> 30) == 0) {
-        if (++spins >= kSpinLimit) {
-          set_status(hdr, kDevTimeout);
-          s = kFlagAgg32;
-          break;
+    bool found = false;
+    while (!found) {
+      uint32_t s[kLbW];
+#pragma unroll
+      for (int k = 0; k < kLbW; ++k) s[k] = (t - k >= 0) ? ld_acq32(stat + (size_t)(t - k) * 256 + d) : kFlagInc32;
+#pragma unroll
+      for (int k = 0; k < kLbW; ++k) {
+        if (!found) {
+          uint32_t spins = 0;
+          while ((s[k] >> 30) == 0) {
+            if (++spins >= kSpinLimit) {
+              set_status(hdr, kDevTimeout);
+              s[k] = kFlagAgg32;
+              break;
+            }
+            s[k] = ld_acq32(stat + (size_t)(t - k) * 256 + d);
+          }
+          excl += s[k] & kValMask32;
+          found = (s[k] >> 30) == 2;
         }
-        s = ld_acq32(stat + (size_t)t * 256 + d);
       }
-      excl += s & kValMask32;
-      if ((s >> 30) == 2) break;
-      --t;
+      t -= kLbW;
     }
     st_rel32(st, kFlagInc32 | (excl + acc));
   }
