@@ -7,8 +7,8 @@
 #include "kernels.cuh"
 
 namespace ubs {
-size_t sort_tile_sizes(uint32_t R, uint32_t NT, uint32_t cap, uint32_t* n_cmp, uint32_t* n_emit, uint32_t* n_rng,
-                       uint32_t* n_dsort, uint32_t* n_isort);
+void sort_tile_sizes(uint32_t R, uint32_t cap, uint32_t* n_cmp, uint32_t* n_emit, uint32_t* n_dsort,
+                     uint32_t* n_isort);
 
 namespace {
 
@@ -87,8 +87,7 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   while ((1ull << bits) < NT) ++bits;
   L.tile_bits = bits;
   L.tile_passes = (bits + 7) / 8;
-  sort_tile_sizes(L.R, L.NT, L.cap, &L.n_cmp_tiles, &L.n_emit_tiles, &L.n_rng_tiles, &L.n_dsort_tiles,
-                  &L.n_isort_tiles);
+  sort_tile_sizes(L.R, L.cap, &L.n_cmp_tiles, &L.n_emit_tiles, &L.n_dsort_tiles, &L.n_isort_tiles);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -111,11 +110,13 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.ikB = take((size_t)L.cap * 4);
   L.ivB = take((size_t)L.cap * 4);
   L.tstart = take((size_t)(L.NT + 1) * 4);
-  // zeroed together at the start of every ubs_bin_sort: scan_stat .. tcount
-  L.scan_stat = take((size_t)(L.n_cmp_tiles + L.n_emit_tiles + L.n_rng_tiles) * 8);
-  L.sort_stat = take(((size_t)4 * L.n_dsort_tiles + (size_t)L.tile_passes * L.n_isort_tiles) * 256 * 4);
+  L.vis_count = take((size_t)L.n_cmp_tiles * 4);
+  L.vis_prefix = take((size_t)L.n_cmp_tiles * 4);
+  // per-pass counts, rewritten whole by every ubs_bin_sort
+  L.hist_d = take((size_t)4 * L.n_dsort_tiles * 256 * 4);
+  L.hist_i = take((size_t)L.tile_passes * L.n_isort_tiles * 256 * 4);
+  L.icount = take((size_t)L.n_emit_tiles * 4);
   L.ghist = take(7 * 256 * 4);
-  L.tcount = take((size_t)L.NT * 4);
   L.Tfin = take((size_t)L.NPIX * 4);
   L.last = take((size_t)L.NPIX * 4);
   L.pairs = take((size_t)L.NPIX * 4);
@@ -214,6 +215,8 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
   if (st != UBS_OK) return st;
   char* w = (char*)ws;
   cudaError_t e = cudaMemsetAsync(w + L.header, 0, sizeof(Header), stream);
+  if (e != cudaSuccess) return UBS_ERR_CUDA;
+  e = cudaMemsetAsync(w + L.vis_count, 0, (size_t)L.n_cmp_tiles * 4, stream);
   if (e != cudaSuccess) return UBS_ERR_CUDA;
   // view table: per-view constants, tile/record/pixel offsets
   ViewDev* views = (ViewDev*)(w + L.views);

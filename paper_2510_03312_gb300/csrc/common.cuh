@@ -80,16 +80,21 @@ struct Layout {
   uint32_t NPIX;    // pixels
   uint32_t cap;     // instance capacity
   int32_t tile_bits, tile_passes;
-  uint32_t n_cmp_tiles;   // compaction scan tiles
-  uint32_t n_emit_tiles;  // emission scan tiles
-  uint32_t n_rng_tiles;   // range scan tiles
+  uint32_t n_cmp_tiles;   // compaction blocks
+  uint32_t n_emit_tiles;  // emission blocks
   uint32_t n_dsort_tiles; // onesweep tiles over records
   uint32_t n_isort_tiles; // onesweep tiles over instances
   size_t header, views, rec4, key, tiles, rect, g2d;
   size_t ckA, cvA, ckB, cvB;
   size_t ikA, ivA, ikB, ivB;
-  size_t tcount, tstart;
-  size_t scan_stat, sort_stat, ghist;
+  size_t tstart;
+  size_t vis_count;  // visible records per compaction block [n_cmp_tiles] (made by preprocess)
+  size_t vis_prefix; // its exclusive prefix [n_cmp_tiles]
+  // rewritten whole by every bin_sort (no zeroing needed)
+  size_t hist_d;     // per (pass block, digit) counts of the 4 depth passes [4][n_dsort_tiles][256]
+  size_t hist_i;     // the same for the tile-key passes [tile_passes][n_isort_tiles][256]
+  size_t icount;     // instances per emission block [n_emit_tiles]
+  size_t ghist;      // digit totals per pass [4 + 3][256]
   size_t Tfin, last, pairs;
   size_t total;
 };
@@ -104,16 +109,11 @@ constexpr int kRecFloats = 12;
 //   [d mu'_x, d mu'_y, d a, d b] [d c, d log2 o(q), d beta_x, d r] [d g, d b, -, -]
 constexpr int kGradFloats = 12;
 
-// status flags of the single-pass (decoupled look-back) scans: top 2 bits
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagInc = 2ull << 62;
-constexpr uint64_t kValMask = (1ull << 62) - 1;
-constexpr uint32_t kFlagAgg32 = 1u << 30;
-constexpr uint32_t kFlagInc32 = 2u << 30;
-constexpr uint32_t kValMask32 = (1u << 30) - 1;
 
-// bounded waits: a look-back gives up after this many polls of one word
-constexpr uint32_t kSpinLimit = 1u << 22;
+// block sizes of the binning kernels (items per block)
+constexpr int kCmpTile = 2048;  // compaction
+constexpr int kOsTile = 4096;   // one radix pass
+constexpr int kEmTile = 1024;   // instance emission
 
 enum DevStatus : uint32_t { kDevOk = 0, kDevCapacity = 3, kDevTimeout = 5, kDevInternal = 6 };
 

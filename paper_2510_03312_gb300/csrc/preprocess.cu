@@ -34,7 +34,7 @@ template <int C>
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList vl, const ViewDev* __restrict__ views,
                                                          CfgDev cfg, float4* __restrict__ rec4,
                                                          uint32_t* __restrict__ key, uint32_t* __restrict__ tiles,
-                                                         uint2* __restrict__ rect) {
+                                                         uint2* __restrict__ rect, uint32_t* __restrict__ vis_count) {
   extern __shared__ ViewDev s_views[];
   for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
   __syncthreads();
@@ -51,6 +51,14 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList v
     view_stage<C>(in, vi, v, cfg, o);
     const uint32_t r = v.rec_off + (uint32_t)p;
     tiles[r] = o.tiles;
+    {
+      // visible records per compaction block (one add per group of lanes)
+      const unsigned act = __activemask();
+      const uint32_t blk = r / kCmpTile;
+      const unsigned peers = __match_any_sync(act, blk);
+      const unsigned vis = __ballot_sync(act, o.valid) & peers;
+      if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1) && vis) atomicAdd(vis_count + blk, (uint32_t)__popc(vis));
+    }
     if (o.valid) {
       key[r] = __float_as_uint(o.depth);
       rect[r] = make_uint2((uint32_t)o.tx0 | ((uint32_t)o.ty0 << 16), (uint32_t)o.tx1 | ((uint32_t)o.ty1 << 16));
@@ -71,11 +79,12 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
   uint32_t* key = (uint32_t*)(ws + L.key);
   uint32_t* tiles = (uint32_t*)(ws + L.tiles);
   uint2* rect = (uint2*)(ws + L.rect);
+  uint32_t* vis = (uint32_t*)(ws + L.vis_count);
   switch (sc.N) {
-    case 3: preprocess_kernel<0><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
-    case 4: preprocess_kernel<1><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
-    case 6: preprocess_kernel<3><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
-    case 7: preprocess_kernel<4><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect); break;
+    case 3: preprocess_kernel<0><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 4: preprocess_kernel<1><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 6: preprocess_kernel<3><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 7: preprocess_kernel<4><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
