@@ -14,13 +14,16 @@
 // the bytes (depth passes touch records, not instances).
 //
 // No kernel waits on another block: every step that needs the offsets of
-// earlier blocks is split at a kernel boundary (reduce, then scan, then
-// place).  A radix pass is an upsweep (each block writes its row of digit
-// counts), a column scan of those rows (each block's exclusive offset per
-// digit, plus the digit totals) and a downsweep (local stable ranking and
-// placement).  The compaction uses visible-record counts per block made by
-// the preprocess kernel; the emission uses instance counts per block of the
-// depth-sorted records.
+// earlier blocks is split at a kernel boundary (count, then scan, then
+// place).  The counts a step needs are made by the kernel before it, while
+// it writes that step's input: the preprocess kernel counts visible records
+// per compaction block; the compaction counts the first depth pass's digits
+// per (pass block, digit); each radix pass counts the next pass's digits for
+// the positions it writes (the last depth pass counts instances per
+// emission block instead); the emission counts the first tile pass's
+// digits.  A column scan turns counts into each block's exclusive offsets
+// (and digit totals), and the pass then ranks its items locally (stable)
+// and places them.
 #include "kernels.cuh"
 
 namespace ubs {
@@ -115,12 +118,13 @@ __global__ void __launch_bounds__(kScT) col_scan_kernel(const uint32_t* in, uint
 constexpr int kCmpT = 256, kCmpI = kCmpTile / kCmpT;
 
 // Keeps the records with tiles_touched > 0, in record order, as (depth key,
-// record) pairs starting at vis_prefix[block].
+// record) pairs starting at vis_prefix[block], and counts the first depth
+// pass's digits per (pass block, digit) into hist0.
 __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restrict__ tiles,
                                                         const uint32_t* __restrict__ key, uint32_t R,
                                                         const uint32_t* __restrict__ vis_prefix,
                                                         uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
-                                                        Header* hdr) {
+                                                        uint32_t* __restrict__ hist0, Header* hdr) {
   __shared__ uint32_t s_w[kCmpT / 32 + 1];
   const uint32_t t = blockIdx.x;
   const uint32_t excl = vis_prefix[t];
@@ -137,15 +141,26 @@ __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restri
   }
   uint32_t total;
   uint32_t pos = excl + block_excl_scan<kCmpT>(cnt, total, s_w);
+  __shared__ uint32_t s_h[2][256];  // the block's items fall in at most two pass blocks
+  for (int i = threadIdx.x; i < 2 * 256; i += kCmpT) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t ob0 = excl / kOsTile;
 #pragma unroll
   for (int i = 0; i < kCmpI; ++i)
     if (f[i]) {
       if (pos < R) {  // holds by construction (counts made by preprocess)
         okey[pos] = k[i];
         oval[pos] = base + i;
+        atomicAdd(&s_h[min(pos / kOsTile - ob0, 1u)][k[i] & 255u], 1u);
       }
       ++pos;
     }
+  __syncthreads();
+  // first depth pass: counts per (pass block, digit)
+  for (int i = threadIdx.x; i < 2 * 256; i += kCmpT) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(hist0 + (size_t)(ob0 + i / 256) * 256 + (i & 255), c);
+  }
   if (t == gridDim.x - 1 && threadIdx.x == 0) hdr->n_visible = excl + total;
 }
 
@@ -153,41 +168,24 @@ __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restri
 
 constexpr int kOsT = 256, kOsI = kOsTile / kOsT, kOsW = kOsT / 32;
 
-// Upsweep of a radix pass: block t writes its counts of the digit at
-// `shift` over items [t kOsTile, (t+1) kOsTile) into row t of hist.
-__global__ void __launch_bounds__(kOsT) upsweep_kernel(const uint32_t* __restrict__ kin, const uint64_t* n_ptr,
-                                                       uint32_t cap, int shift, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_h[256];
-  const uint64_t n64 = *n_ptr;
-  const uint32_t n = (uint32_t)(n64 < cap ? n64 : cap);
-  const uint32_t t = blockIdx.x;
-  s_h[threadIdx.x] = 0;
-  __syncthreads();
-  const uint32_t tile_base = t * kOsTile;
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  if (tile_base < n) {
-    const uint32_t wbase = tile_base + warp * (kOsI * 32);
-#pragma unroll 4
-    for (int i = 0; i < kOsI; ++i) {
-      const uint32_t idx = wbase + i * 32 + lane;
-      const uint32_t d = idx < n ? (kin[idx] >> shift) & 255u : 0x100u;
-      const uint32_t peers = peer_mask(d);
-      if (d < 256 && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
-    }
-  }
-  __syncthreads();
-  hist[(size_t)t * 256 + threadIdx.x] = s_h[threadIdx.x];
-}
-
-// Downsweep of a radix pass over the 8 bits at `shift`: stable local ranking
-// and placement at ghist-exclusive-prefix + hprefix[block][digit] + rank.
+// One stable pass of the LSD radix sort over the 8 bits at `shift`: local
+// ranking, placement at (exclusive prefix of ghist) + hprefix[block][digit]
+// + rank, and, while placing, the counts the following step needs:
 //   ghist:   digit totals of this pass over all n items
-//   hprefix: [blocks][256] exclusive column prefix of the upsweep counts
+//   hprefix: [blocks][256] exclusive column prefix of this pass's
+//            per-(block, digit) counts
+//   hnext:   if non-null, counts of the next pass's digit (at shift + 8) per
+//            (output block, digit)
+//   icount:  if non-null, instances (tiles_touched of each placed record)
+//            per emission block of the output
+// The counts are summed over lanes with equal (block, digit) before one
+// atomic add per group.
 __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                                                          uint32_t* __restrict__ vout, const uint64_t* n_ptr,
                                                          uint32_t cap, int shift, const uint32_t* __restrict__ ghist,
-                                                         const uint32_t* __restrict__ hprefix) {
+                                                         const uint32_t* __restrict__ hprefix, uint32_t* hnext,
+                                                         uint32_t* icount, const uint32_t* __restrict__ tiles_touched) {
   __shared__ uint32_t s_keys[kOsTile];
   __shared__ uint32_t s_vals[kOsTile];
   __shared__ uint32_t s_hist[kOsW][256];
@@ -252,12 +250,32 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
   }
   __syncthreads();
   const uint32_t cnt_tile = (n - tile_base) < (uint32_t)kOsTile ? (n - tile_base) : (uint32_t)kOsTile;
-  for (uint32_t j = threadIdx.x; j < cnt_tile; j += kOsT) {
-    const uint32_t key = s_keys[j];
-    const uint32_t g = s_goff[(key >> shift) & 255u] + j;
-    if (g < n) {  // holds by construction (consistent digit counts)
-      kout[g] = key;
-      vout[g] = s_vals[j];
+#pragma unroll 4
+  for (int it = 0; it < kOsI; ++it) {
+    const uint32_t j = it * kOsT + threadIdx.x;
+    bool valid = j < cnt_tile;
+    uint32_t key = 0, val = 0, g = 0;
+    if (valid) {
+      key = s_keys[j];
+      val = s_vals[j];
+      g = s_goff[(key >> shift) & 255u] + j;
+      valid = g < n;  // holds by construction (consistent digit counts)
+      if (valid) {
+        kout[g] = key;
+        vout[g] = val;
+      }
+    }
+    if (hnext) {
+      const uint32_t grp = valid ? ((g / kOsTile) << 8) | ((key >> (shift + 8)) & 255u) : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(kFull, grp);
+      if (valid && lane == (uint32_t)(__ffs(peers) - 1))
+        atomicAdd(hnext + (size_t)(grp >> 8) * 256 + (grp & 255u), (uint32_t)__popc(peers));
+    }
+    if (icount) {
+      const uint32_t grp = valid ? g / kEmTile : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(kFull, grp);
+      const uint32_t sum = __reduce_add_sync(peers, valid ? tiles_touched[val] : 0u);
+      if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(icount + grp, sum);
     }
   }
 }
@@ -267,31 +285,17 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
 constexpr int kEmT = 256, kEmI = kEmTile / kEmT;
 
 // Instances of the depth-sorted records of emission block t (row t of icount).
-__global__ void __launch_bounds__(kEmT) icount_kernel(const uint32_t* __restrict__ srec,
-                                                      const uint32_t* __restrict__ tiles, const Header* hdr,
-                                                      uint32_t* __restrict__ icount) {
-  __shared__ uint32_t s_w[kEmT / 32 + 1];
-  const uint64_t n = hdr->n_visible;
-  const uint32_t base = blockIdx.x * kEmTile + threadIdx.x * kEmI;
-  uint32_t sum = 0;
-#pragma unroll
-  for (int i = 0; i < kEmI; ++i)
-    if (base + i < n) sum += tiles[srec[base + i]];
-  uint32_t total;
-  block_excl_scan<kEmT>(sum, total, s_w);
-  if (threadIdx.x == 0) icount[blockIdx.x] = total;
-}
-
 // For the depth-sorted visible records, writes each record's tiles (row-major
 // within its rectangle) as (global tile, record) instances from
-// icount_prefix[block] on.
+// icount_prefix[block] on, and counts the first tile pass's digits per
+// (pass block, digit) into hist0.
 __global__ void __launch_bounds__(kEmT) emit_kernel(const uint32_t* __restrict__ srec,
                                                     const uint32_t* __restrict__ tiles,
                                                     const uint2* __restrict__ rect,
                                                     const ViewDev* __restrict__ views, int V, uint32_t cap,
                                                     const uint32_t* __restrict__ icount_prefix,
                                                     uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-                                                    Header* hdr) {
+                                                    uint32_t* __restrict__ hist0, Header* hdr) {
   __shared__ uint32_t s_rec[kEmTile];
   __shared__ uint32_t s_off[kEmTile + 1];
   __shared__ uint2 s_rect[kEmTile];
@@ -344,25 +348,38 @@ __global__ void __launch_bounds__(kEmT) emit_kernel(const uint32_t* __restrict__
   __syncthreads();
   const uint64_t excl = icount_prefix[t];
   bool overflow = false;
-  for (uint32_t j = threadIdx.x; j < total; j += kEmT) {
-    int lo = 0, hi = kEmTile - 1;  // last item with s_off <= j
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+  const uint32_t lane = lane_id();
+  for (uint32_t j0 = 0; j0 < total; j0 += kEmT) {
+    const uint32_t j = j0 + threadIdx.x;
+    bool valid = false;
+    uint32_t gt = 0;
+    uint64_t pos = 0;
+    if (j < total) {
+      int lo = 0, hi = kEmTile - 1;  // last item with s_off <= j
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+      }
+      const uint32_t local = j - s_off[lo];
+      const uint2 rc = s_rect[lo];
+      const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
+      const uint32_t w = x1 - x0;
+      const uint32_t tx = x0 + local % w, ty = y0 + local / w;
+      gt = s_vtile[lo] + ty * s_vtx[lo] + tx;
+      pos = excl + j;
+      if (pos < cap) {
+        ikey[pos] = gt;
+        ival[pos] = s_rec[lo];
+        valid = true;
+      } else {
+        overflow = true;
+      }
     }
-    const uint32_t local = j - s_off[lo];
-    const uint2 rc = s_rect[lo];
-    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
-    const uint32_t w = x1 - x0;
-    const uint32_t tx = x0 + local % w, ty = y0 + local / w;
-    const uint32_t gt = s_vtile[lo] + ty * s_vtx[lo] + tx;
-    const uint64_t pos = excl + j;
-    if (pos < cap) {
-      ikey[pos] = gt;
-      ival[pos] = s_rec[lo];
-    } else {
-      overflow = true;
-    }
+    // first tile pass: counts per (pass block, digit), one add per lane group
+    const uint32_t grp = valid ? ((uint32_t)(pos / kOsTile) << 8) | (gt & 255u) : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(kFull, grp);
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1))
+      atomicAdd(hist0 + (size_t)(grp >> 8) * 256 + (grp & 255u), (uint32_t)__popc(peers));
   }
   if (overflow) set_status(hdr, kDevCapacity);
   if ((uint64_t)t == n_tiles - 1 && threadIdx.x == 0) hdr->n_inst = excl + total;
@@ -394,6 +411,9 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   (void)cfg;
   Header* hdr = (Header*)(ws + L.header);
   if (L.R == 0) return cudaMemsetAsync(ws + L.tstart, 0, (size_t)(L.NT + 1) * 4, st);
+  // the per-pass counts are accumulated with atomics: start them at zero
+  cudaError_t e = cudaMemsetAsync(ws + L.hist_d, 0, L.Tfin - L.hist_d, st);
+  if (e != cudaSuccess) return e;
   const uint32_t* vis = (const uint32_t*)(ws + L.vis_count);
   uint32_t* vis_prefix = (uint32_t*)(ws + L.vis_prefix);
   uint32_t* hd = (uint32_t*)(ws + L.hist_d);
@@ -406,38 +426,40 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* ckB = (uint32_t*)(ws + L.ckB);
   uint32_t* cvB = (uint32_t*)(ws + L.cvB);
   col_scan_kernel<<<1, kScT, 0, st>>>(vis, vis_prefix, L.n_cmp_tiles, 1, nullptr);
-  compact_kernel<<<L.n_cmp_tiles, kCmpT, 0, st>>>(tiles, (const uint32_t*)(ws + L.key), L.R, vis_prefix, ckA, cvA,
-                                                  hdr);
-  // depth sort: 4 passes A->B->A->B->A
   const size_t hd_stride = (size_t)L.n_dsort_tiles * 256;
+  compact_kernel<<<L.n_cmp_tiles, kCmpT, 0, st>>>(tiles, (const uint32_t*)(ws + L.key), L.R, vis_prefix, ckA, cvA,
+                                                  hd, hdr);
+  // depth sort: 4 passes A->B->A->B->A; the last one counts instances per
+  // emission block
   for (int p = 0; p < 4; ++p) {
     const bool even = (p & 1) == 0;
-    const uint32_t* kin = even ? ckA : ckB;
     uint32_t* hp = hd + p * hd_stride;
-    upsweep_kernel<<<L.n_dsort_tiles, kOsT, 0, st>>>(kin, &hdr->n_visible, L.R, 8 * p, hp);
+    const bool last = p == 3;
     col_scan_kernel<<<256, kScT, 0, st>>>(hp, hp, L.n_dsort_tiles, 256, ghist + 256 * p);
-    downsweep_kernel<<<L.n_dsort_tiles, kOsT, 0, st>>>(kin, even ? cvA : cvB, even ? ckB : ckA, even ? cvB : cvA,
-                                                       &hdr->n_visible, L.R, 8 * p, ghist + 256 * p, hp);
+    downsweep_kernel<<<L.n_dsort_tiles, kOsT, 0, st>>>(even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
+                                                       even ? cvB : cvA, &hdr->n_visible, L.R, 8 * p, ghist + 256 * p,
+                                                       hp, last ? nullptr : hp + hd_stride, last ? icount : nullptr,
+                                                       tiles);
   }
   uint32_t* ikA = (uint32_t*)(ws + L.ikA);
   uint32_t* ivA = (uint32_t*)(ws + L.ivA);
   uint32_t* ikB = (uint32_t*)(ws + L.ikB);
   uint32_t* ivB = (uint32_t*)(ws + L.ivB);
   const ViewDev* views = (const ViewDev*)(ws + L.views);
-  icount_kernel<<<L.n_emit_tiles, kEmT, 0, st>>>(cvA, tiles, hdr, icount);
   col_scan_kernel<<<1, kScT, 0, st>>>(icount, icount, L.n_emit_tiles, 1, nullptr);
   emit_kernel<<<L.n_emit_tiles, kEmT, 0, st>>>(cvA, tiles, (const uint2*)(ws + L.rect), views, L.V, L.cap, icount,
-                                               ikA, ivA, hdr);
+                                               ikA, ivA, hi, hdr);
   uint32_t* gh_tile = ghist + 4 * 256;
   const size_t hi_stride = (size_t)L.n_isort_tiles * 256;
   for (int p = 0; p < L.tile_passes; ++p) {
     const bool even = (p & 1) == 0;
-    const uint32_t* kin = even ? ikA : ikB;
     uint32_t* hp = hi + p * hi_stride;
-    upsweep_kernel<<<L.n_isort_tiles, kOsT, 0, st>>>(kin, &hdr->n_inst, L.cap, 8 * p, hp);
+    const bool last = p == L.tile_passes - 1;
     col_scan_kernel<<<256, kScT, 0, st>>>(hp, hp, L.n_isort_tiles, 256, gh_tile + 256 * p);
-    downsweep_kernel<<<L.n_isort_tiles, kOsT, 0, st>>>(kin, even ? ivA : ivB, even ? ikB : ikA, even ? ivB : ivA,
-                                                       &hdr->n_inst, L.cap, 8 * p, gh_tile + 256 * p, hp);
+    downsweep_kernel<<<L.n_isort_tiles, kOsT, 0, st>>>(even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
+                                                       even ? ivB : ivA, &hdr->n_inst, L.cap, 8 * p,
+                                                       gh_tile + 256 * p, hp, last ? nullptr : hp + hi_stride,
+                                                       nullptr, nullptr);
   }
   const uint32_t* skeys = (const uint32_t*)(ws + ((L.tile_passes & 1) ? L.ikB : L.ikA));
   ranges_kernel<<<592, 256, 0, st>>>(skeys, &hdr->n_inst, L.cap, L.NT, (uint32_t*)(ws + L.tstart));
