@@ -170,7 +170,9 @@ def kernels_per_step(r):
     tile_passes = (bits + 7) // 8
     upload = (V + 15) // 16
     pre = upload + S
-    sort = 1 + 4 + 1 + 1 + tile_passes
+    # scan, compact, 4 depth passes (scan + downsweep), scan, emit, tile-key
+    # passes (scan + downsweep), ranges
+    sort = 2 + 4 * 2 + 2 + 2 * tile_passes + 1
     return pre + sort + 1 + 1 + S
 
 

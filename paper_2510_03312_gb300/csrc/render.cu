@@ -1,13 +1,17 @@
 // render.cu -- R1 (forward blend) and G1 (backward blend).
 //
-// One CTA per screen tile, one thread per pixel; each warp owns an 8x4 pixel
-// block of the tile.  The tile's front-to-back list (sorted record ids) is
-// consumed in batches of up to 256 records: each batch's 48-byte render
-// records are staged in shared memory together with a conservative screen
-// box of each record's support (the ellipse r <= r_cut, r_cut the radius
-// beyond which alpha < alpha_min, widened by a margin).  A warp skips a
-// record whose box misses its block -- a warp-uniform branch that can only
-// drop pairs whose alpha is below alpha_min, so no decision changes.
+// One CTA per screen tile.  In the forward each warp owns an 8x4 pixel block
+// of the tile, one pixel per lane; in the backward an 8x8 block, two pixels
+// per lane (rows y and y + 4), which halves the per-entry warp reductions
+// there.  (Two pixels per lane made the forward slower: its per-pixel early
+// termination then diverges within a lane.)  The tile's front-to-back
+// list (sorted record ids) is consumed in batches of up to 256 records: each
+// batch's 48-byte render records are staged in shared memory together with
+// a conservative screen box of each record's support (the ellipse
+// r <= r_cut, r_cut the radius beyond which alpha < alpha_min, widened by a
+// margin).  Each warp first lists the batch entries whose box meets its
+// block (32 boxes per ballot) and then walks only that list -- a cull that
+// can only drop pairs whose alpha is below alpha_min, so no decision changes.
 //
 // Per pair (Sec. 3, Eq. r; Sec. 4.3 final density), with the screen mean
 // staged relative to the tile origin o as m = (hi - o) + lo:
@@ -20,16 +24,14 @@
 // backward kernel re-derives exactly the forward's alpha and decisions.
 // A CTA stops loading batches once every pixel of the tile has terminated.
 //
-// Each warp first lists the batch entries whose box meets its block (32 boxes
-// per ballot), then walks only that list, two entries at a time.
-//
 // The backward walks each tile's list back to front from the last
 // contributor, recovers T by division and forms per-pair gradients of
-// (mu', conic, log2 o(q), beta_x, rgb).  They are summed over the warp's
-// lanes with a transposed butterfly (reduce-scatter: 12 shuffles for the 10
-// values, leaving each total in one lane), added per record in shared memory
-// across the CTA's warps, and flushed with one vector atomic add per
-// (record, tile) -- never one global atomic per pixel.
+// (mu', conic, log2 o(q), beta_x, rgb).  A lane first adds its two pixels'
+// contributions; the warp then sums its lanes with a transposed butterfly
+// (reduce-scatter: 12 shuffles for the 10 values, leaving each total in one
+// lane), the CTA's warps add per record in shared memory, and one vector
+// atomic add per (record, tile) flushes the sum -- never one global atomic
+// per pixel.
 #include "kernels.cuh"
 
 namespace ubs {
@@ -37,6 +39,9 @@ namespace ubs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// backward: pixels per lane (rows y and y + 4 of the warp's 8x8 block); four
+// per lane (8x16 blocks) measured 1.6x slower, at 97 registers
+constexpr int kBwdPPT = 2;
 
 __device__ __forceinline__ float lg2_approx(float x) {
   float y;
@@ -53,9 +58,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // the tile origin (hi - origin) + lo, exact for the subtraction and rounded
 // once, so that per pair dx = (pixel centre - origin) - mean costs one add.
 struct Staged {
-  float4 p;   // mean_x, mean_y (tile-relative), a, 2b
-  float4 q;   // c, log2 o(q), beta_x, red
-  float2 s;   // green, blue
+  float4 p;  // mean_x, mean_y (tile-relative), a, 2b
+  float4 q;  // c, log2 o(q), beta_x, red
+  float2 s;  // green, blue
 };
 
 __device__ __forceinline__ void stage_record(const float4* __restrict__ rec4, uint32_t r, float ox, float oy,
@@ -109,13 +114,14 @@ __device__ __forceinline__ int find_view(const ViewDev* __restrict__ views, int 
   return lo;
 }
 
-// pixel of this thread: warps tile the TWxTH tile with 8x4 blocks
-template <int TW>
+// the warp's 8 x RB block (bx, by) within a TW-wide tile and this lane's
+// first pixel (lx, ly); with RB = 8 the lane's second pixel is (lx, ly + 4)
+template <int TW, int RB>
 __device__ __forceinline__ void pixel_of(int& lx, int& ly, int& bx, int& by) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int WPR = TW / 8;  // warps per row of blocks
   bx = (w % WPR) * 8;
-  by = (w / WPR) * 4;
+  by = (w / WPR) * RB;
   lx = bx + (lane & 7);
   ly = by + (lane >> 3);
 }
@@ -163,7 +169,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
   int lx, ly, bx, by;
-  pixel_of<TW>(lx, ly, bx, by);
+  pixel_of<TW, 4>(lx, ly, bx, by);
   const int x = tx * TW + lx, y = ty * TH + ly;
   const bool inside = x < v.W && y < v.H;
   const float ox = (float)(tx * TW), oy = (float)(ty * TH);
@@ -302,15 +308,15 @@ __device__ __forceinline__ int writer_of(int lane) {
 //   v7..9 = sum alpha T dL/dC.
 // With dr = -beta q:  d mu' = 2 beta [[a, b], [b, c]] (v0, v1),
 // d(a, b, c) = -beta (v2, 2 v3, v4), d log2 o = ln2 v5, d beta = ln2 v6.
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 8))
+template <int TW, int TH, int kPPT>
+__global__ void __launch_bounds__(TW * TH / kPPT)
     render_bwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       const float* __restrict__ dLdimg, const float* __restrict__ Tfin,
                       const uint32_t* __restrict__ lastc, float4* __restrict__ g2d, const Header* hdr, uint32_t R) {
-  constexpr int B = TW * TH;
-  constexpr int BS = B < 256 ? B : 256;  // records staged per batch
-  constexpr int NW = B / 32;
+  constexpr int NT = TW * TH / kPPT;  // threads
+  constexpr int BS = 256;             // records staged per batch
+  constexpr int NW = NT / 32;
   __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
   __shared__ float2 s_s[BS];
   __shared__ uint32_t s_rec[BS];
@@ -325,39 +331,50 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     s_v = find_view(views, V, g);
     s_max = 0;
   }
-  for (int i = threadIdx.x; i < 10 * (BS + 1); i += B) (&s_acc[0][0])[i] = 0.0f;
-  if (threadIdx.x < BS) s_hit[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < 10 * (BS + 1); i += NT) (&s_acc[0][0])[i] = 0.0f;
+  for (int i = threadIdx.x; i < BS; i += NT) s_hit[i] = 0;
   __syncthreads();
   const ViewDev& v = views[s_v];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
   int lx, ly, bx, by;
-  pixel_of<TW>(lx, ly, bx, by);
-  const int x = tx * TW + lx, y = ty * TH + ly;
-  const bool inside = x < v.W && y < v.H;
+  pixel_of<TW, 4 * kPPT>(lx, ly, bx, by);
   const float ox = (float)(tx * TW), oy = (float)(ty * TH);
-  const float fx = (float)lx + 0.5f, fy = (float)ly + 0.5f;
-  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 3.0f;
+  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + (float)(4 * kPPT - 1);
   const float lg2_amin = lg2_approx(cfg.amin);
   uint8_t* list = s_list[threadIdx.x >> 5];
   const uint32_t start = tstart[g];
   const int lane = threadIdx.x & 31;
   const int wslot = writer_of(lane);
-  float T = 1.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f;
-  uint32_t last = 0;
-  if (inside) {
-    const size_t plane = (size_t)v.W * v.H;
-    const size_t pix = (size_t)y * v.W + x;
-    const float* gi = dLdimg + (size_t)v.pix_off * 3;
-    G0 = gi[pix];
-    G1 = gi[plane + pix];
-    G2 = gi[2 * plane + pix];
-    T = Tfin[v.pix_off + pix];
-    last = lastc[v.pix_off + pix];
+  const int x = tx * TW + lx;
+  const float fx = (float)lx + 0.5f;
+  float fy[kPPT], T[kPPT], G0[kPPT], G1[kPPT], G2[kPPT], B0[kPPT], B1[kPPT], B2[kPPT];
+  uint32_t last[kPPT];
+  uint32_t mylast = 0;
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    const int y = ty * TH + ly + 4 * k;
+    fy[k] = (float)(ly + 4 * k) + 0.5f;
+    T[k] = 1.0f;
+    G0[k] = G1[k] = G2[k] = 0.0f;
+    last[k] = 0;
+    if (x < v.W && y < v.H) {
+      const size_t plane = (size_t)v.W * v.H;
+      const size_t pix = (size_t)y * v.W + x;
+      const float* gi = dLdimg + (size_t)v.pix_off * 3;
+      G0[k] = gi[pix];
+      G1[k] = gi[plane + pix];
+      G2[k] = gi[2 * plane + pix];
+      T[k] = Tfin[v.pix_off + pix];
+      last[k] = lastc[v.pix_off + pix];
+    }
+    // colour behind the current record, normalised by the transmittance after it
+    B0[k] = cfg.bg[0];
+    B1[k] = cfg.bg[1];
+    B2[k] = cfg.bg[2];
+    mylast = max(mylast, last[k]);
   }
-  // colour behind the current record, normalised by the transmittance after it
-  float B0 = cfg.bg[0], B1 = cfg.bg[1], B2 = cfg.bg[2];
-  const uint32_t wlast = __reduce_max_sync(kFull, last);
+  const uint32_t wlast = __reduce_max_sync(kFull, mylast);
   if (lane == 0 && wlast) atomicMax(&s_max, wlast);
   __syncthreads();
   const uint32_t nmax = s_max;
@@ -366,16 +383,16 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     const int lo = hi - BS > 0 ? hi - BS : 0;
     const int n = hi - lo;
     __syncthreads();
-    if ((int)threadIdx.x < n) {
-      const uint32_t r = min(ivals[start + lo + threadIdx.x], R - 1);  // ids are < R by construction
+    for (int s = threadIdx.x; s < n; s += NT) {
+      const uint32_t r = min(ivals[start + lo + s], R - 1);  // ids are < R by construction
       Staged st;
       float4 box;
       stage_record(rec4, r, ox, oy, lg2_amin, st, box);
-      s_rec[threadIdx.x] = r;
-      s_p[threadIdx.x] = st.p;
-      s_q[threadIdx.x] = st.q;
-      s_s[threadIdx.x] = st.s;
-      s_bb[threadIdx.x] = box;
+      s_rec[s] = r;
+      s_p[s] = st.p;
+      s_q[s] = st.q;
+      s_s[s] = st.s;
+      s_bb[s] = box;
     }
     __syncthreads();
     // entries past every lane's last contributor are not listed
@@ -383,47 +400,47 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     const int cnt = warp_cull_list(s_bb, nw, false, wx0, wx1, wy0, wy1, list);
     for (int i = cnt - 1; i >= 0; --i) {
       const int j = list[i];
+      const float4 p = s_p[j], q = s_q[j];
+      const float2 c2 = s_s[j];
       float gv[10];
-      bool hit = false;
-      if ((uint32_t)(lo + j) < last) {
-        const float4 p = s_p[j], q = s_q[j];
+#pragma unroll
+      for (int m = 0; m < 10; ++m) gv[m] = 0.0f;
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k) {
         PairEval e;
-        eval_pair(fx, fy, p, q, cfg.amin, cfg.amax, e);
-        if (e.use) {
-          hit = true;
-          const float2 c2 = s_s[j];
-          const float inv = __frcp_rn(e.om);  // 1 / (1 - r)
-          T = __fdividef(T, 1.0f - e.alpha);   // transmittance before this record
-          const float w = e.alpha * T;
-          gv[7] = w * G0;
-          gv[8] = w * G1;
-          gv[9] = w * G2;
-          const float d0 = q.w - B0, d1 = c2.x - B1, d2 = c2.y - B2;
-          const float dalpha = T * fmaf(d0, G0, fmaf(d1, G1, d2 * G2));
-          B0 = fmaf(e.alpha, d0, B0);
-          B1 = fmaf(e.alpha, d1, B1);
-          B2 = fmaf(e.alpha, d2, B2);
-          const float ga = e.alpha < cfg.amax ? dalpha * e.alpha : 0.0f;
-          const float qq = ga * inv;
-          gv[0] = qq * e.dx;
-          gv[1] = qq * e.dy;
-          gv[2] = gv[0] * e.dx;
-          gv[3] = gv[0] * e.dy;
-          gv[4] = gv[1] * e.dy;
-          gv[5] = ga;
-          gv[6] = ga * e.lg;
-        }
+        eval_pair(fx, fy[k], p, q, cfg.amin, cfg.amax, e);
+        // branch-free: pairs the forward skipped contribute zero and leave T, B
+        const bool use = e.use && (uint32_t)(lo + j) < last[k];
+        any = any || use;
+        const float a = use ? e.alpha : 0.0f;
+        T[k] = __fdividef(T[k], 1.0f - a);  // transmittance before this record
+        const float w = a * T[k];
+        gv[7] = fmaf(w, G0[k], gv[7]);
+        gv[8] = fmaf(w, G1[k], gv[8]);
+        gv[9] = fmaf(w, G2[k], gv[9]);
+        const float d0 = q.w - B0[k], d1 = c2.x - B1[k], d2 = c2.y - B2[k];
+        const float dalpha = T[k] * fmaf(d0, G0[k], fmaf(d1, G1[k], d2 * G2[k]));
+        B0[k] = fmaf(a, d0, B0[k]);
+        B1[k] = fmaf(a, d1, B1[k]);
+        B2[k] = fmaf(a, d2, B2[k]);
+        const float ga = a < cfg.amax ? dalpha * a : 0.0f;
+        const float qq = use ? ga * __frcp_rn(e.om) : 0.0f;
+        const float u0 = qq * e.dx, u1 = qq * e.dy;
+        gv[0] += u0;
+        gv[1] += u1;
+        gv[2] = fmaf(u0, e.dx, gv[2]);
+        gv[3] = fmaf(u0, e.dy, gv[3]);
+        gv[4] = fmaf(u1, e.dy, gv[4]);
+        gv[5] += ga;
+        gv[6] = fmaf(ga, use ? e.lg : 0.0f, gv[6]);
       }
-      const unsigned hits = __ballot_sync(kFull, hit);
+      const unsigned hits = __ballot_sync(kFull, any);
       if (hits == 0) continue;
-      if (!hit) {
-#pragma unroll
-        for (int k = 0; k < 10; ++k) gv[k] = 0.0f;
-      }
       if (__popc(hits) == 1) {  // one lane: its values are the totals
-        if (hit) {
+        if (any) {
 #pragma unroll
-          for (int k = 0; k < 10; ++k) atomicAdd(&s_acc[k][j], gv[k]);
+          for (int m = 0; m < 10; ++m) atomicAdd(&s_acc[m][j], gv[m]);
           s_hit[j] = 1;
         }
       } else {
@@ -433,8 +450,8 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
       }
     }
     __syncthreads();
-    if ((int)threadIdx.x < n && s_hit[threadIdx.x]) {
-      const int j = threadIdx.x;
+    for (int j = threadIdx.x; j < n; j += NT) {
+      if (!s_hit[j]) continue;
       const float4 p = s_p[j], q = s_q[j];
       const float a = p.z, b = 0.5f * p.w, c = q.x, beta = q.z;
       const float v0 = s_acc[0][j], v1 = s_acc[1][j];
@@ -444,7 +461,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
       atomicAdd(dst + 1, make_float4(-beta * s_acc[4][j], kLn2f * s_acc[5][j], kLn2f * s_acc[6][j], s_acc[7][j]));
       atomicAdd((float2*)(dst + 2), make_float2(s_acc[8][j], s_acc[9][j]));
 #pragma unroll
-      for (int k = 0; k < 10; ++k) s_acc[k][j] = 0.0f;
+      for (int m = 0; m < 10; ++m) s_acc[m][j] = 0.0f;
       s_hit[j] = 0;
     }
   }
@@ -459,19 +476,19 @@ cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cu
   uint32_t* last = (uint32_t*)(ws + L.last);
   const Header* hdr = (const Header*)(ws + L.header);
   const uint32_t R = L.R > 0 ? L.R : 1;
+  constexpr int NT = TW * TH;
   if (cfg.flags & 2)  // diagnostic variant: also count visited pairs with r < 1 per pixel
-    render_fwd_kernel<TW, TH, true><<<L.NT, TW * TH, 0, st>>>(views, L.V, cfg, tstart, sorted_instances(L, ws),
-                                                            rec4, image, Tfin, last, hdr, R,
-                                                            (uint32_t*)(ws + L.pairs));
+    render_fwd_kernel<TW, TH, true><<<L.NT, NT, 0, st>>>(views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
+                                                       image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs));
   else
-    render_fwd_kernel<TW, TH, false><<<L.NT, TW * TH, 0, st>>>(views, L.V, cfg, tstart, sorted_instances(L, ws),
-                                                             rec4, image, Tfin, last, hdr, R, nullptr);
+    render_fwd_kernel<TW, TH, false><<<L.NT, NT, 0, st>>>(views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
+                                                        image, Tfin, last, hdr, R, nullptr);
   return cudaGetLastError();
 }
 
 template <int TW, int TH>
 cudaError_t bwd_t(const Layout& L, const CfgDev& cfg, char* ws, const float* dL, cudaStream_t st) {
-  render_bwd_kernel<TW, TH><<<L.NT, TW * TH, 0, st>>>(
+  render_bwd_kernel<TW, TH, kBwdPPT><<<L.NT, TW * TH / kBwdPPT, 0, st>>>(
       (const ViewDev*)(ws + L.views), L.V, cfg, (const uint32_t*)(ws + L.tstart), sorted_instances(L, ws),
       (const float4*)(ws + L.rec4), dL, (const float*)(ws + L.Tfin), (const uint32_t*)(ws + L.last),
       (float4*)(ws + L.g2d), (const Header*)(ws + L.header), L.R > 0 ? L.R : 1);
