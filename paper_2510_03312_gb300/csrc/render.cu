@@ -64,7 +64,7 @@ struct Staged {
 };
 
 __device__ __forceinline__ void stage_record(const float4* __restrict__ rec4, uint32_t r, float ox, float oy,
-                                             float lg2_amin, Staged& st, float4& box) {
+                                             float lg2_amin, Staged& st, float4& box, float& rcut) {
   const float4 a = rec4[3 * (size_t)r], c = rec4[3 * (size_t)r + 1], d = rec4[3 * (size_t)r + 2];
   st.p = make_float4(__fadd_rn(__fsub_rn(a.x, ox), a.z), __fadd_rn(__fsub_rn(a.y, oy), a.w), c.x,
                      __fmul_rn(2.0f, c.y));
@@ -78,8 +78,10 @@ __device__ __forceinline__ void stage_record(const float4* __restrict__ rec4, ui
   float rc = 1.0f - ex2_approx((lg2_amin - c.w) / d.x);
   if (!(rc > -0.02f)) {
     box = make_float4(1.0f, -1.0f, 1.0f, -1.0f);
+    rcut = -1.0f;
   } else {
     rc = fminf(1.0f, fmaf(rc, 1.02f, 0.02f));
+    rcut = rc;
     const float ex = sqrtf(fmaxf(rc * s00, 0.0f)) + 0.1f, ey = sqrtf(fmaxf(rc * s11, 0.0f)) + 0.1f;
     box = make_float4(st.p.x - ex, st.p.x + ex, st.p.y - ey, st.p.y + ey);
   }
@@ -130,16 +132,38 @@ __device__ __forceinline__ bool box_hits(const float4& bb, float x0, float x1, f
   return bb.x <= x1 && bb.y >= x0 && bb.z <= y1 && bb.w >= y0;
 }
 
-// Each warp lists, in order, the staged entries j < n whose box meets its
-// block (all of them when `all`); returns the count.
-__device__ __forceinline__ int warp_cull_list(const float4* s_bb, int n, bool all, float x0, float x1, float y0,
+// Whether the ellipse r <= rcut meets the rectangle [x0, x1] x [y0, y1]:
+// the smallest r = a dx^2 + 2b dx dy + c dy^2 over the rectangle is 0 when it
+// holds the mean, else it lies on an edge, where r is a 1-D convex quadratic
+// minimised by clamping its stationary point to the edge.  Rounding here is
+// far inside the margin by which rcut was widened.
+__device__ __forceinline__ bool ellipse_hits(const float4& p, float c, float rcut, float x0, float x1, float y0,
+                                             float y1) {
+  const float dx0 = x0 - p.x, dx1 = x1 - p.x, dy0 = y0 - p.y, dy1 = y1 - p.y;
+  const float a = p.z, b2 = p.w, hb = 0.5f * p.w;  // b2 = 2b
+  const float ia = __frcp_rn(a), ic = __frcp_rn(c);
+  auto rq = [&](float dx, float dy) { return fmaf(dx, fmaf(a, dx, b2 * dy), c * dy * dy); };
+  float m = rq(dx0, fminf(fmaxf(-hb * dx0 * ic, dy0), dy1));
+  m = fminf(m, rq(dx1, fminf(fmaxf(-hb * dx1 * ic, dy0), dy1)));
+  m = fminf(m, rq(fminf(fmaxf(-hb * dy0 * ia, dx0), dx1), dy0));
+  m = fminf(m, rq(fminf(fmaxf(-hb * dy1 * ia, dx0), dx1), dy1));
+  const bool inside = dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f;
+  return inside || m <= rcut;
+}
+
+// Each warp lists, in order, the staged entries j < n whose support meets
+// its block (all of them when `all`): the box test, then the exact ellipse
+// test; returns the count.
+__device__ __forceinline__ int warp_cull_list(const float4* s_bb, const float4* s_p, const float4* s_q,
+                                              const float* s_rc, int n, bool all, float x0, float x1, float y0,
                                               float y1, uint8_t* list) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int cnt = 0;
   for (int k = 0; k < n; k += 32) {
     const int j = k + lane;
-    const bool hit = j < n && (all || box_hits(s_bb[j], x0, x1, y0, y1));
+    bool hit = j < n && (all || box_hits(s_bb[j], x0, x1, y0, y1));
+    if (hit && !all) hit = ellipse_hits(s_p[j], s_q[j].x, s_rc[j], x0, x1, y0, y1);
     const unsigned m = __ballot_sync(kFull, hit);
     if (hit) list[cnt + __popc(m & lt)] = (uint8_t)j;
     cnt += __popc(m);
@@ -159,6 +183,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
   constexpr int NW = B / 32;
   __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
   __shared__ float2 s_s[BS];
+  __shared__ float s_rc[BS];
   __shared__ uint8_t s_list[NW][BS];
   __shared__ int s_v;
   if (hdr->status != 0) return;
@@ -187,7 +212,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     if (threadIdx.x < BS && idx < end) {
       Staged st;
       float4 box;
-      stage_record(rec4, min(ivals[idx], R - 1), ox, oy, lg2_amin, st, box);  // ids are < R by construction
+      stage_record(rec4, min(ivals[idx], R - 1), ox, oy, lg2_amin, st, box, s_rc[threadIdx.x]);  // ids < R
       s_p[threadIdx.x] = st.p;
       s_q[threadIdx.x] = st.q;
       s_s[threadIdx.x] = st.s;
@@ -196,7 +221,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     __syncthreads();
     const int n = (int)min((uint32_t)BS, end - base);
     // the counting variant visits every pair with r < 1
-    const int cnt = warp_cull_list(s_bb, n, COUNT, wx0, wx1, wy0, wy1, list);
+    const int cnt = warp_cull_list(s_bb, s_p, s_q, s_rc, n, COUNT, wx0, wx1, wy0, wy1, list);
     const uint32_t rel = base - start;
     for (int i = 0; i < cnt; i += 2) {
       if (__all_sync(kFull, done)) break;
@@ -319,6 +344,7 @@ __global__ void __launch_bounds__(TW * TH / kPPT)
   constexpr int NW = NT / 32;
   __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
   __shared__ float2 s_s[BS];
+  __shared__ float s_rc[BS];
   __shared__ uint32_t s_rec[BS];
   __shared__ float s_acc[10][BS + 1];  // +1: the 10 writer lanes hit 10 different banks
   __shared__ int s_hit[BS];
@@ -387,7 +413,7 @@ __global__ void __launch_bounds__(TW * TH / kPPT)
       const uint32_t r = min(ivals[start + lo + s], R - 1);  // ids are < R by construction
       Staged st;
       float4 box;
-      stage_record(rec4, r, ox, oy, lg2_amin, st, box);
+      stage_record(rec4, r, ox, oy, lg2_amin, st, box, s_rc[s]);
       s_rec[s] = r;
       s_p[s] = st.p;
       s_q[s] = st.q;
@@ -397,7 +423,7 @@ __global__ void __launch_bounds__(TW * TH / kPPT)
     __syncthreads();
     // entries past every lane's last contributor are not listed
     const int nw = max(0, min(n, (int)wlast - lo));
-    const int cnt = warp_cull_list(s_bb, nw, false, wx0, wx1, wy0, wy1, list);
+    const int cnt = warp_cull_list(s_bb, s_p, s_q, s_rc, nw, false, wx0, wx1, wy0, wy1, list);
     for (int i = cnt - 1; i >= 0; --i) {
       const int j = list[i];
       const float4 p = s_p[j], q = s_q[j];
