@@ -428,18 +428,23 @@ __global__ void __launch_bounds__(TW * TH / kPPT)
       const int j = list[i];
       const float4 p = s_p[j], q = s_q[j];
       const float2 c2 = s_s[j];
+      PairEval e[kPPT];
+      bool use[kPPT], any = false;
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k) {
+        eval_pair(fx, fy[k], p, q, cfg.amin, cfg.amax, e[k]);
+        use[k] = e[k].use && (uint32_t)(lo + j) < last[k];  // pairs the forward composited
+        any = any || use[k];
+      }
+      const unsigned hits = __ballot_sync(kFull, any);
+      if (hits == 0) continue;  // no pixel of the block: T and B stay
       float gv[10];
 #pragma unroll
       for (int m = 0; m < 10; ++m) gv[m] = 0.0f;
-      bool any = false;
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
-        PairEval e;
-        eval_pair(fx, fy[k], p, q, cfg.amin, cfg.amax, e);
-        // branch-free: pairs the forward skipped contribute zero and leave T, B
-        const bool use = e.use && (uint32_t)(lo + j) < last[k];
-        any = any || use;
-        const float a = use ? e.alpha : 0.0f;
+        // branch-free: a pair the forward skipped contributes zero and leaves T, B
+        const float a = use[k] ? e[k].alpha : 0.0f;
         T[k] = __fdividef(T[k], 1.0f - a);  // transmittance before this record
         const float w = a * T[k];
         gv[7] = fmaf(w, G0[k], gv[7]);
@@ -451,18 +456,16 @@ __global__ void __launch_bounds__(TW * TH / kPPT)
         B1[k] = fmaf(a, d1, B1[k]);
         B2[k] = fmaf(a, d2, B2[k]);
         const float ga = a < cfg.amax ? dalpha * a : 0.0f;
-        const float qq = use ? ga * __frcp_rn(e.om) : 0.0f;
-        const float u0 = qq * e.dx, u1 = qq * e.dy;
+        const float qq = use[k] ? __fdividef(ga, e[k].om) : 0.0f;  // 1 - r > 0 for a composited pair
+        const float u0 = qq * e[k].dx, u1 = qq * e[k].dy;
         gv[0] += u0;
         gv[1] += u1;
-        gv[2] = fmaf(u0, e.dx, gv[2]);
-        gv[3] = fmaf(u0, e.dy, gv[3]);
-        gv[4] = fmaf(u1, e.dy, gv[4]);
+        gv[2] = fmaf(u0, e[k].dx, gv[2]);
+        gv[3] = fmaf(u0, e[k].dy, gv[3]);
+        gv[4] = fmaf(u1, e[k].dy, gv[4]);
         gv[5] += ga;
-        gv[6] = fmaf(ga, use ? e.lg : 0.0f, gv[6]);
+        gv[6] = fmaf(ga, use[k] ? e[k].lg : 0.0f, gv[6]);
       }
-      const unsigned hits = __ballot_sync(kFull, any);
-      if (hits == 0) continue;
       if (__popc(hits) == 1) {  // one lane: its values are the totals
         if (any) {
 #pragma unroll
