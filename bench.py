@@ -170,9 +170,9 @@ def kernels_per_step(r):
     tile_passes = (bits + 7) // 8
     upload = (V + 15) // 16
     pre = upload + S
-    # scan, compact, 4 depth passes (scan + downsweep), scan, emit, tile-key
-    # passes (scan + downsweep), ranges
-    sort = 2 + 4 * 2 + 2 + 2 * tile_passes + 1
+    # scan, compact, 4 depth passes (scan + downsweep), scan, emission offsets
+    # and fill, tile-key passes (scan + downsweep), ranges
+    sort = 2 + 4 * 2 + 3 + 2 * tile_passes + 1
     return pre + sort + 1 + 1 + S
 
 

@@ -112,6 +112,7 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.tstart = take((size_t)(L.NT + 1) * 4);
   L.vis_count = take((size_t)L.n_cmp_tiles * 4);
   L.vis_prefix = take((size_t)L.n_cmp_tiles * 4);
+  L.ioff = take((size_t)L.R * 4);
   // per-pass counts, rewritten whole by every ubs_bin_sort
   L.hist_d = take((size_t)4 * L.n_dsort_tiles * 256 * 4);
   L.hist_i = take((size_t)L.tile_passes * L.n_isort_tiles * 256 * 4);

@@ -81,15 +81,16 @@ struct Layout {
   uint32_t cap;     // instance capacity
   int32_t tile_bits, tile_passes;
   uint32_t n_cmp_tiles;   // compaction blocks
-  uint32_t n_emit_tiles;  // emission blocks
-  uint32_t n_dsort_tiles; // onesweep tiles over records
-  uint32_t n_isort_tiles; // onesweep tiles over instances
+  uint32_t n_emit_tiles;  // emission offset blocks (records)
+  uint32_t n_dsort_tiles; // depth radix pass blocks (records)
+  uint32_t n_isort_tiles; // tile-key radix pass blocks = emission fill blocks (instances)
   size_t header, views, rec4, key, tiles, rect, g2d;
   size_t ckA, cvA, ckB, cvB;
   size_t ikA, ivA, ikB, ivB;
   size_t tstart;
   size_t vis_count;  // visible records per compaction block [n_cmp_tiles] (made by preprocess)
   size_t vis_prefix; // its exclusive prefix [n_cmp_tiles]
+  size_t ioff;       // first instance of each depth-sorted record [R]
   // rewritten whole by every bin_sort (no zeroing needed)
   size_t hist_d;     // per (pass block, digit) counts of the 4 depth passes [4][n_dsort_tiles][256]
   size_t hist_i;     // the same for the tile-key passes [tile_passes][n_isort_tiles][256]
@@ -112,8 +113,9 @@ constexpr int kGradFloats = 12;
 
 // block sizes of the binning kernels (items per block)
 constexpr int kCmpTile = 2048;  // compaction
-constexpr int kOsTile = 4096;   // one radix pass
-constexpr int kEmTile = 1024;   // instance emission
+constexpr int kDsTile = 2048;   // one depth radix pass (records)
+constexpr int kIsTile = 2048;   // one tile-key radix pass and one emission fill block (instances)
+constexpr int kEmTile = 1024;   // instance offsets of the depth-sorted records
 
 enum DevStatus : uint32_t { kDevOk = 0, kDevCapacity = 3, kDevTimeout = 5, kDevInternal = 6 };
 

@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(kScT) col_scan_kernel(const uint32_t* in, uint
 // ---------------------------------------------------------------- compaction
 
 constexpr int kCmpT = 256, kCmpI = kCmpTile / kCmpT;
+// depth pass blocks that kCmpTile consecutive output positions can fall in
+constexpr int kCmpSpan = (kCmpTile + kDsTile - 1) / kDsTile + 1;
 
 // Keeps the records with tiles_touched > 0, in record order, as (depth key,
 // record) pairs starting at vis_prefix[block], and counts the first depth
@@ -141,23 +143,23 @@ __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restri
   }
   uint32_t total;
   uint32_t pos = excl + block_excl_scan<kCmpT>(cnt, total, s_w);
-  __shared__ uint32_t s_h[2][256];  // the block's items fall in at most two pass blocks
-  for (int i = threadIdx.x; i < 2 * 256; i += kCmpT) (&s_h[0][0])[i] = 0;
+  __shared__ uint32_t s_h[kCmpSpan][256];
+  for (int i = threadIdx.x; i < kCmpSpan * 256; i += kCmpT) (&s_h[0][0])[i] = 0;
   __syncthreads();
-  const uint32_t ob0 = excl / kOsTile;
+  const uint32_t ob0 = excl / kDsTile;
 #pragma unroll
   for (int i = 0; i < kCmpI; ++i)
     if (f[i]) {
       if (pos < R) {  // holds by construction (counts made by preprocess)
         okey[pos] = k[i];
         oval[pos] = base + i;
-        atomicAdd(&s_h[min(pos / kOsTile - ob0, 1u)][k[i] & 255u], 1u);
+        atomicAdd(&s_h[min(pos / kDsTile - ob0, (uint32_t)kCmpSpan - 1u)][k[i] & 255u], 1u);
       }
       ++pos;
     }
   __syncthreads();
   // first depth pass: counts per (pass block, digit)
-  for (int i = threadIdx.x; i < 2 * 256; i += kCmpT) {
+  for (int i = threadIdx.x; i < kCmpSpan * 256; i += kCmpT) {
     const uint32_t c = (&s_h[0][0])[i];
     if (c) atomicAdd(hist0 + (size_t)(ob0 + i / 256) * 256 + (i & 255), c);
   }
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restri
 
 // ---------------------------------------------------------------- radix pass
 
-constexpr int kOsT = 256, kOsI = kOsTile / kOsT, kOsW = kOsT / 32;
+constexpr int kOsT = 256, kOsW = kOsT / 32;
 
 // One stable pass of the LSD radix sort over the 8 bits at `shift`: local
 // ranking, placement at (exclusive prefix of ghist) + hprefix[block][digit]
@@ -179,15 +181,17 @@ constexpr int kOsT = 256, kOsI = kOsTile / kOsT, kOsW = kOsT / 32;
 //   icount:  if non-null, instances (tiles_touched of each placed record)
 //            per emission block of the output
 // The counts are summed over lanes with equal (block, digit) before one
-// atomic add per group.
+// atomic add per group.  A block ranks TILE items.
+template <int TILE>
 __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                                                          uint32_t* __restrict__ vout, const uint64_t* n_ptr,
                                                          uint32_t cap, int shift, const uint32_t* __restrict__ ghist,
                                                          const uint32_t* __restrict__ hprefix, uint32_t* hnext,
                                                          uint32_t* icount, const uint32_t* __restrict__ tiles_touched) {
-  __shared__ uint32_t s_keys[kOsTile];
-  __shared__ uint32_t s_vals[kOsTile];
+  constexpr int kOsI = TILE / kOsT;
+  __shared__ uint32_t s_keys[TILE];
+  __shared__ uint32_t s_vals[TILE];
   __shared__ uint32_t s_hist[kOsW][256];
   __shared__ uint32_t s_boff[256];
   __shared__ uint32_t s_goff[256];
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
   const uint64_t n64 = *n_ptr;
   const uint32_t n = (uint32_t)(n64 < cap ? n64 : cap);
   const uint32_t t = blockIdx.x;
-  const uint32_t tile_base = t * kOsTile;
+  const uint32_t tile_base = t * TILE;
   if (tile_base >= n) return;
   for (int i = threadIdx.x; i < kOsW * 256; i += kOsT) (&s_hist[0][0])[i] = 0;
   __syncthreads();
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
     }
   }
   __syncthreads();
-  const uint32_t cnt_tile = (n - tile_base) < (uint32_t)kOsTile ? (n - tile_base) : (uint32_t)kOsTile;
+  const uint32_t cnt_tile = (n - tile_base) < (uint32_t)TILE ? (n - tile_base) : (uint32_t)TILE;
 #pragma unroll 4
   for (int it = 0; it < kOsI; ++it) {
     const uint32_t j = it * kOsT + threadIdx.x;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
       }
     }
     if (hnext) {
-      const uint32_t grp = valid ? ((g / kOsTile) << 8) | ((key >> (shift + 8)) & 255u) : 0xffffffffu;
+      const uint32_t grp = valid ? ((g / TILE) << 8) | ((key >> (shift + 8)) & 255u) : 0xffffffffu;
       const uint32_t peers = __match_any_sync(kFull, grp);
       if (valid && lane == (uint32_t)(__ffs(peers) - 1))
         atomicAdd(hnext + (size_t)(grp >> 8) * 256 + (grp & 255u), (uint32_t)__popc(peers));
@@ -284,105 +288,143 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
 
 constexpr int kEmT = 256, kEmI = kEmTile / kEmT;
 
-// Instances of the depth-sorted records of emission block t (row t of icount).
-// For the depth-sorted visible records, writes each record's tiles (row-major
-// within its rectangle) as (global tile, record) instances from
-// icount_prefix[block] on, and counts the first tile pass's digits per
-// (pass block, digit) into hist0.
-__global__ void __launch_bounds__(kEmT) emit_kernel(const uint32_t* __restrict__ srec,
-                                                    const uint32_t* __restrict__ tiles,
-                                                    const uint2* __restrict__ rect,
-                                                    const ViewDev* __restrict__ views, int V, uint32_t cap,
-                                                    const uint32_t* __restrict__ icount_prefix,
-                                                    uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-                                                    uint32_t* __restrict__ hist0, Header* hdr) {
-  __shared__ uint32_t s_rec[kEmTile];
-  __shared__ uint32_t s_off[kEmTile + 1];
-  __shared__ uint2 s_rect[kEmTile];
-  __shared__ uint32_t s_vtile[kEmTile];
-  __shared__ uint32_t s_vtx[kEmTile];
-  __shared__ uint32_t s_recoff[kMaxViews], s_tileoff[kMaxViews], s_tilesx[kMaxViews];
+// First instance of each depth-sorted record: ioff[i] = icount_prefix[block]
+// + the exclusive scan of tiles_touched within the block.  The last block
+// records the instance total and flags an instance capacity overflow.
+__global__ void __launch_bounds__(kEmT) emit_offsets_kernel(const uint32_t* __restrict__ srec,
+                                                            const uint32_t* __restrict__ tiles,
+                                                            const uint32_t* __restrict__ icount_prefix,
+                                                            uint32_t* __restrict__ ioff, uint32_t cap, Header* hdr) {
   __shared__ uint32_t s_w[kEmT / 32 + 1];
-  const uint64_t n = hdr->n_visible;
+  const uint32_t n = (uint32_t)hdr->n_visible;
   const uint32_t t = blockIdx.x;
-  const uint64_t n_tiles = (n + kEmTile - 1) / kEmTile;
-  if ((uint64_t)t >= n_tiles) return;
-  for (int i = threadIdx.x; i < V; i += kEmT) {
+  const uint32_t n_blocks = (n + kEmTile - 1) / kEmTile;
+  if (t >= n_blocks) return;
+  const uint32_t base = t * kEmTile + threadIdx.x * kEmI;
+  uint32_t c[kEmI], sum = 0;
+#pragma unroll
+  for (int i = 0; i < kEmI; ++i) {
+    c[i] = base + i < n ? tiles[srec[base + i]] : 0u;
+    sum += c[i];
+  }
+  uint32_t total;
+  uint32_t ex = icount_prefix[t] + block_excl_scan<kEmT>(sum, total, s_w);
+#pragma unroll
+  for (int i = 0; i < kEmI; ++i) {
+    if (base + i < n) ioff[base + i] = ex;
+    ex += c[i];
+  }
+  if (t == n_blocks - 1 && threadIdx.x == 0) {
+    const uint64_t n_inst = (uint64_t)icount_prefix[t] + total;
+    hdr->n_inst = n_inst;
+    if (n_inst > cap) set_status(hdr, kDevCapacity);
+  }
+}
+
+constexpr int kFlT = 256, kFlI = kIsTile / kFlT;
+
+// Instances [b K, (b + 1) K) of the depth-sorted order, K = kIsTile: block b
+// of the first tile-key pass, so that every block does the same work however
+// unevenly the instances fall over the records.  Instance j belongs to the
+// sorted record i with ioff[i] <= j < ioff[i + 1] and is that record's
+// (j - ioff[i])-th tile, row-major in its rectangle; it is written as
+// (global tile, record).  ioff strictly increases (every visible record
+// touches a tile), so the records holding the block's instances are the K
+// from the one holding its first instance on.  Writes the first tile pass's
+// digit counts of the block.
+__global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restrict__ srec,
+                                                         const uint32_t* __restrict__ ioff,
+                                                         const uint2* __restrict__ rect,
+                                                         const ViewDev* __restrict__ views, int V, uint32_t cap,
+                                                         uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
+                                                         uint32_t* __restrict__ hist0, const Header* hdr) {
+  __shared__ uint32_t s_off[kIsTile + 1];
+  __shared__ uint32_t s_h[256];
+  __shared__ uint32_t s_recoff[kMaxViews], s_tileoff[kMaxViews], s_tilesx[kMaxViews];
+  __shared__ uint32_t s_r0;
+  const uint32_t nv = (uint32_t)hdr->n_visible;
+  const uint64_t ni64 = hdr->n_inst;
+  const uint32_t n_inst = (uint32_t)(ni64 < cap ? ni64 : cap);
+  const uint32_t s = blockIdx.x * kIsTile;
+  if (s >= n_inst || nv == 0) return;
+  for (int i = threadIdx.x; i < 256; i += kFlT) s_h[i] = 0;
+  for (int i = threadIdx.x; i < V; i += kFlT) {
     s_recoff[i] = views[i].rec_off;
     s_tileoff[i] = views[i].tile_off;
     s_tilesx[i] = (uint32_t)views[i].tiles_x;
   }
-  __syncthreads();
-  const uint32_t base = t * kEmTile + threadIdx.x * kEmI;
-  uint32_t c[kEmI];
-  uint32_t tsum = 0;
-#pragma unroll
-  for (int i = 0; i < kEmI; ++i) {
-    const uint32_t idx = base + i;
-    const uint32_t slot = threadIdx.x * kEmI + i;
-    uint32_t r = 0;
-    c[i] = 0;
-    if (idx < n) {
-      r = srec[idx];
-      c[i] = tiles[r];
-      s_rect[slot] = rect[r];
-      int lo = 0, hi = V - 1;  // view of record r: last view with rec_off <= r
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_recoff[mid] <= r) lo = mid; else hi = mid - 1;
-      }
-      s_vtile[slot] = s_tileoff[lo];
-      s_vtx[slot] = s_tilesx[lo];
+  if (threadIdx.x < 32) {
+    // the last sorted record with ioff <= s, by a 32-way search: each round
+    // samples 32 offsets of [lo, hi) and keeps the span after the last one
+    // <= s (ioff[0] = 0 <= s, so lane 0's sample always qualifies)
+    const uint32_t lane = threadIdx.x;
+    uint32_t lo = 0, hi = nv;
+    while (hi - lo > 32) {
+      const uint32_t step = (hi - lo + 31) / 32;
+      const uint32_t idx = lo + lane * step;
+      const uint32_t m = __ballot_sync(kFull, idx < hi && ioff[idx] <= s);
+      lo += (31u - __clz(m)) * step;
+      hi = min(hi, lo + step);
     }
-    s_rec[slot] = r;
-    tsum += c[i];
+    const uint32_t idx = lo + lane;
+    const uint32_t m = __ballot_sync(kFull, idx < hi && ioff[idx] <= s);
+    if (lane == 0) s_r0 = lo + 31u - __clz(m);
   }
-  uint32_t total;
-  uint32_t ex = block_excl_scan<kEmT>(tsum, total, s_w);
-#pragma unroll
-  for (int i = 0; i < kEmI; ++i) {
-    s_off[threadIdx.x * kEmI + i] = ex;
-    ex += c[i];
-  }
-  if (threadIdx.x == 0) s_off[kEmTile] = total;
   __syncthreads();
-  const uint64_t excl = icount_prefix[t];
-  bool overflow = false;
-  const uint32_t lane = lane_id();
-  for (uint32_t j0 = 0; j0 < total; j0 += kEmT) {
-    const uint32_t j = j0 + threadIdx.x;
-    bool valid = false;
-    uint32_t gt = 0;
-    uint64_t pos = 0;
-    if (j < total) {
-      int lo = 0, hi = kEmTile - 1;  // last item with s_off <= j
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+  const uint32_t r0 = s_r0;
+  for (uint32_t i = threadIdx.x; i <= (uint32_t)kIsTile; i += kFlT)
+    s_off[i] = r0 + i < nv ? ioff[r0 + i] : 0xffffffffu;
+  __syncthreads();
+  // kFlI consecutive instances per thread, walking the records
+  const uint32_t j0 = s + threadIdx.x * kFlI;
+  if (j0 < n_inst) {
+    int lo = 0, hi = kIsTile - 1;  // last i with s_off[i] <= j0 (s_off[0] <= s, s_off[K] > s + K - 1)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= j0) lo = mid; else hi = mid - 1;
+    }
+    uint32_t i = (uint32_t)lo;
+    uint32_t rec = 0, x0 = 0, x1 = 0, tx = 0, ty = 0, vt = 0, vx = 0;
+    bool fresh = true;
+    for (int k = 0; k < kFlI; ++k) {
+      const uint32_t j = j0 + k;
+      if (j >= n_inst) break;
+      while (s_off[i + 1] <= j) {  // stays below K: s_off[K] > j
+        ++i;
+        fresh = true;
       }
-      const uint32_t local = j - s_off[lo];
-      const uint2 rc = s_rect[lo];
-      const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
-      const uint32_t w = x1 - x0;
-      const uint32_t tx = x0 + local % w, ty = y0 + local / w;
-      gt = s_vtile[lo] + ty * s_vtx[lo] + tx;
-      pos = excl + j;
-      if (pos < cap) {
-        ikey[pos] = gt;
-        ival[pos] = s_rec[lo];
-        valid = true;
-      } else {
-        overflow = true;
+      if (fresh) {
+        fresh = false;
+        rec = srec[r0 + i];
+        const uint2 rc = rect[rec];
+        x0 = rc.x & 0xFFFFu;
+        x1 = rc.y & 0xFFFFu;
+        const uint32_t w = x1 - x0, local = j - s_off[i];
+        tx = x0 + local % w;
+        ty = (rc.x >> 16) + local / w;
+        int vlo = 0, vhi = V - 1;  // view of the record: last view with rec_off <= rec
+        while (vlo < vhi) {
+          const int mid = (vlo + vhi + 1) >> 1;
+          if (s_recoff[mid] <= rec) vlo = mid; else vhi = mid - 1;
+        }
+        vt = s_tileoff[vlo];
+        vx = s_tilesx[vlo];
+      }
+      const uint32_t gt = vt + ty * vx + tx;
+      ikey[j] = gt;
+      ival[j] = rec;
+      atomicAdd(&s_h[gt & 255u], 1u);
+      if (++tx == x1) {
+        tx = x0;
+        ++ty;
       }
     }
-    // first tile pass: counts per (pass block, digit), one add per lane group
-    const uint32_t grp = valid ? ((uint32_t)(pos / kOsTile) << 8) | (gt & 255u) : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(kFull, grp);
-    if (valid && lane == (uint32_t)(__ffs(peers) - 1))
-      atomicAdd(hist0 + (size_t)(grp >> 8) * 256 + (grp & 255u), (uint32_t)__popc(peers));
   }
-  if (overflow) set_status(hdr, kDevCapacity);
-  if ((uint64_t)t == n_tiles - 1 && threadIdx.x == 0) hdr->n_inst = excl + total;
+  __syncthreads();
+  // this block is block blockIdx.x of the first tile pass: its counts are
+  // written whole (no pass and no counts when the problem has one tile)
+  if (hist0)
+    for (int d = threadIdx.x; d < 256; d += kFlT) hist0[(size_t)blockIdx.x * 256 + d] = s_h[d];
 }
 
 // ---------------------------------------------------------------- ranges
@@ -436,7 +478,7 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
     uint32_t* hp = hd + p * hd_stride;
     const bool last = p == 3;
     col_scan_kernel<<<256, kScT, 0, st>>>(hp, hp, L.n_dsort_tiles, 256, ghist + 256 * p);
-    downsweep_kernel<<<L.n_dsort_tiles, kOsT, 0, st>>>(even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
+    downsweep_kernel<kDsTile><<<L.n_dsort_tiles, kOsT, 0, st>>>(even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
                                                        even ? cvB : cvA, &hdr->n_visible, L.R, 8 * p, ghist + 256 * p,
                                                        hp, last ? nullptr : hp + hd_stride, last ? icount : nullptr,
                                                        tiles);
@@ -447,8 +489,10 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* ivB = (uint32_t*)(ws + L.ivB);
   const ViewDev* views = (const ViewDev*)(ws + L.views);
   col_scan_kernel<<<1, kScT, 0, st>>>(icount, icount, L.n_emit_tiles, 1, nullptr);
-  emit_kernel<<<L.n_emit_tiles, kEmT, 0, st>>>(cvA, tiles, (const uint2*)(ws + L.rect), views, L.V, L.cap, icount,
-                                               ikA, ivA, hi, hdr);
+  uint32_t* ioff = (uint32_t*)(ws + L.ioff);
+  emit_offsets_kernel<<<L.n_emit_tiles, kEmT, 0, st>>>(cvA, tiles, icount, ioff, L.cap, hdr);
+  emit_fill_kernel<<<L.n_isort_tiles, kFlT, 0, st>>>(cvA, ioff, (const uint2*)(ws + L.rect), views, L.V, L.cap,
+                                                     ikA, ivA, L.tile_passes > 0 ? hi : nullptr, hdr);
   uint32_t* gh_tile = ghist + 4 * 256;
   const size_t hi_stride = (size_t)L.n_isort_tiles * 256;
   for (int p = 0; p < L.tile_passes; ++p) {
@@ -456,7 +500,7 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
     uint32_t* hp = hi + p * hi_stride;
     const bool last = p == L.tile_passes - 1;
     col_scan_kernel<<<256, kScT, 0, st>>>(hp, hp, L.n_isort_tiles, 256, gh_tile + 256 * p);
-    downsweep_kernel<<<L.n_isort_tiles, kOsT, 0, st>>>(even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
+    downsweep_kernel<kIsTile><<<L.n_isort_tiles, kOsT, 0, st>>>(even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
                                                        even ? ivB : ivA, &hdr->n_inst, L.cap, 8 * p,
                                                        gh_tile + 256 * p, hp, last ? nullptr : hp + hi_stride,
                                                        nullptr, nullptr);
@@ -470,8 +514,8 @@ void sort_tile_sizes(uint32_t R, uint32_t cap, uint32_t* n_cmp, uint32_t* n_emit
                      uint32_t* n_isort) {
   *n_cmp = (R + kCmpTile - 1) / kCmpTile;
   *n_emit = (R + kEmTile - 1) / kEmTile;
-  *n_dsort = (R + kOsTile - 1) / kOsTile;
-  *n_isort = (cap + kOsTile - 1) / kOsTile;
+  *n_dsort = (R + kDsTile - 1) / kDsTile;
+  *n_isort = (cap + kIsTile - 1) / kIsTile;
 }
 
 }  // namespace ubs

@@ -142,6 +142,43 @@ def test_large_screen_filling_primitive():
     check_grads(gpu, orc, ref)
 
 
+def test_single_tile_problem():
+    """One tile in the whole problem: no tile-key radix pass at all."""
+    sc = S.make_scene(62, 3, 600, means="uniform", extent=0.5, scale_range=(0.05, 0.4))
+    R, t = S.look_at((0.0, 0.0, -2.5))
+    v = S.make_view(R, t, 16, 16)
+    cfg = S.RasterConfig()
+    orc = R64.Oracle([sc], [v], cfg)
+    gpu = gpu_forward([sc], [v], cfg)
+    assert gpu["status"].instances > 0
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    _, _, ref = check_images(gpu, orc, recs=recs)
+    check_grads(gpu, orc, ref)
+
+
+def test_records_spanning_emission_blocks():
+    """Primitives that each touch thousands of tiles, among many small ones:
+    one record's instances cross the 4096-instance emission blocks."""
+    big = S.make_scene(63, 3, 6, means="uniform", extent=0.05, scale_range=(0.8, 1.6))
+    small = S.make_scene(64, 3, 3000, means="uniform", extent=1.0, scale_range=(0.01, 0.05))
+    sc = S.Scene(3, big.rot_mode, np.ascontiguousarray(np.concatenate([big.params, small.params], axis=1)))
+    R, t = S.look_at((0.0, 0.0, -2.0))
+    v = S.make_view(R, t, 2048, 2048)
+    cfg = S.RasterConfig()
+    orc = R64.Oracle([sc], [v], cfg)
+    gpu = gpu_forward([sc], [v], cfg)
+    counts = orc.pre32[0]["tiles_touched"]
+    assert counts.max() > 4096
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    rng = np.random.default_rng(1)
+    n_tiles = orc.bins["ranges"].shape[0]
+    tiles = sorted(rng.choice(n_tiles, 6, replace=False).tolist())
+    _, _, ref = check_images(gpu, orc, recs=recs, tiles=tiles)
+    check_grads(gpu, orc, ref, tiles=tiles)
+
+
 def test_full_size_static_sampled():
     """The 1M-primitive 1600x1060 workload in the launch configuration the
     benchmark times: all records and instance lists bit-exact, images and
