@@ -176,6 +176,51 @@ def kernels_per_step(r):
     return pre + sort + 1 + 1 + S
 
 
+def step_rooflines(stage_ms, names, params_bytes, R, instances, NT, pairs, pk, n_sm):
+    """Every stage against its bound, with the algorithmic work per unit of
+    the design notes: preprocess reads the parameters once and writes 44 B
+    per record; the sort moves 12 B per instance for emission, 24 B per
+    instance per pass of an LSD sort over (tile, depth) keys
+    (ceil((tile bits + 32) / 8) passes) and 8 B per instance for the ranges;
+    the forward blend costs 16 FP32 + 2 MUFU operations per pair, the
+    backward blend 45 FP32 + 3 MUFU; the parameter backward reads the
+    parameters and 40 B of screen gradients per record and writes the
+    parameter gradients.  t_roof is the time at the peak of the binding
+    unit; the path fraction is sum(t_roof) / measured step time."""
+    hbm = pk["hbm_gbs"] * 1e9
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32 = n_sm * 128 * mhz * 1e6
+    mufu = n_sm * 16 * mhz * 1e6
+    tile_bits = max(1, math.ceil(math.log2(max(NT, 2))))
+    passes = math.ceil((tile_bits + 32) / 8)
+    work = {
+        "preprocess": ("hbm", params_bytes + 44 * R),
+        "bin_sort": ("hbm", instances * (12 + 24 * passes + 8)),
+        "render_fwd": ("alu", (16 * pairs, 2 * pairs)),
+        "render_bwd_blend": ("alu", (45 * pairs, 3 * pairs)),
+        "render_bwd_params": ("hbm", 2 * params_bytes + 40 * R),
+    }
+    out, t_roof = {}, 0.0
+    for n, ms in zip(names, stage_ms):
+        bound, w = work[n]
+        t = ms * 1e-3
+        if bound == "hbm":
+            tr = w / hbm
+            out[n] = {"bound": "hbm", "bytes": int(w), "achieved": round(w / t / 1e9, 1), "peak": pk["hbm_gbs"],
+                      "unit": "GB/s", "frac": round(tr / t, 4)}
+        else:
+            tr = max(w[0] / fp32, w[1] / mufu)
+            out[n] = {"bound": "alu", "fp32_ops": int(w[0]), "mufu_ops": int(w[1]),
+                      "achieved": round(w[0] / t / 1e12, 3), "peak": round(fp32 / 1e12, 2), "unit": "TFLOP/s",
+                      "frac": round(tr / t, 4)}
+        out[n]["ms"] = round(float(ms), 4)
+        t_roof += tr
+    total = float(sum(stage_ms)) * 1e-3
+    path = {"t_roof_ms": round(t_roof * 1e3, 4), "t_ms": round(total * 1e3, 4), "frac": round(t_roof / total, 4),
+            "sort_passes_counted": passes}
+    return out, path
+
+
 def bench_ours(args, rank, world, local):
     import torch
 
@@ -283,6 +328,31 @@ def bench_ours(args, rank, world, local):
             roof = {"bound": "hbm", "kernel": names[dom], "achieved": round(ach, 1),
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
                     "traffic": traffic_record(names[dom])}
+    params_bytes = ds.params.numel() * 4
+    steps_roof, path_roof = step_rooflines(stage_mean, names, params_bytes, sc.P * len(wl.views),
+                                           int(st.instances), r.n_tiles(), pairs, pk, n_sm)
+    # the same step replayed as one captured CUDA graph (L2 flushed between steps)
+    graph = r.capture(dL)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    g_ms = []
+    for i in range(args.steps):
+        flush.fill_((i + 3) & 0xFF)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        g_ms.append((e0, e1))
+    torch.cuda.synchronize()
+    g_total = float(sum(a.elapsed_time(b) for a, b in g_ms))
+    if dist:
+        t = torch.tensor([g_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        g_total = float(t.item())
+    graph_out = {"ms_per_step": round(g_total / args.steps, 4),
+                 "value": round(world * args.steps * mp_per_view / (g_total / 1e3), 2)}
+    del graph
     # end to end through the public API with host buffers
     e2e = bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view)
     out = {
@@ -298,6 +368,9 @@ def bench_ours(args, rank, world, local):
         "views_per_sec": round(world * args.steps / (total_ms / 1e3), 2),
         "stage_ms": {n: round(float(m), 4) for n, m in zip(names, stage_mean)},
         "roofline": roof,
+        "roofline_steps": steps_roof,
+        "roofline_path": path_roof,
+        "graph": graph_out,
         "e2e": e2e,
         "gpu_launches": kernels_per_step(r) * args.steps,
         "clocks": clk,
@@ -353,49 +426,75 @@ def bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view):
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": round(ms / args.steps, 4)}
 
 
-def bench_batched(dev, steps=10, warmup=3):
-    """View-dependent (N=6, 500K, 16 x 1280x720) and dynamic (N=7, 300K,
-    8 x 1352x1014) workloads: all views in one problem against one problem
-    per view launched back to back, forward+backward."""
+def time_calls(fn, steps, warmup):
+    """Milliseconds per call of fn() (CUDA events on the current stream)."""
     import torch
 
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_batched(dev, steps=5, warmup=2):
+    """Batches of views, forward+backward per step:
+      view-dependent N=6, 500K primitives, 16 x 1280x720;
+      dynamic N=7, 300K primitives, 8 (camera, time) x 1352x1014;
+      uneven mix, 64 jobs over 8 scenes (N in {3,6,7}, 10K-2M primitives,
+      256x256 to 1920x1080).
+    Forms: per_view = one problem per view launched back to back (the plain
+    form); batched_one_launch = all views in one problem, 16x16 tiles, eager;
+    batched = the autotuned tile shape and schedule with the whole step
+    replayed as one captured CUDA graph.  Gradients of each scene are summed
+    over its views in every form."""
+    import torch
+
+    from paper_2510_03312_gb300 import autotune as A
     from paper_2510_03312_gb300 import raster
     from paper_2510_03312_gb300 import scenes as S
 
     res = {}
-    for wl in (S.workload_view_dependent(), S.workload_dynamic()):
-        ds = raster.DeviceScene.from_scene(wl.scenes[0], device=dev)
+    for make in (S.workload_view_dependent, S.workload_dynamic, S.workload_uneven_mix):
+        wl = make()
+        ds = [raster.DeviceScene.from_scene(sc, device=dev) for sc in wl.scenes]
         mp = sum(v.width * v.height for v in wl.views) / 1e6
-        batched = raster.Rasterizer([ds], wl.views, wl.cfg, device=dev)
-        singles = [raster.Rasterizer([ds], [v], wl.cfg, device=dev) for v in wl.views]
-        out = {}
-        for mode, rs in (("batched", [batched]), ("per_view", singles)):
-            dls = []
-            for r in rs:
-                img = r.forward(check=True)
-                dls.append(torch.full_like(img, 1.0 / img.numel()))
-            torch.cuda.synchronize()
+        nv = len(wl.views)
+        out = {"views": nv, "megapixels": round(mp, 3), "primitives": [sc.P for sc in wl.scenes]}
 
-            def step():
-                for r, d in zip(rs, dls):
-                    r.forward(check=False)
-                    r.backward(d)
+        def entry(ms):
+            return {"ms_per_step": round(ms, 4), "MP_per_s": round(mp / (ms / 1e3), 2),
+                    "views_per_s": round(nv / (ms / 1e3), 2)}
 
-            for _ in range(warmup):
-                step()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(steps):
-                step()
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
-            out[mode] = {"ms_per_step": round(ms, 4), "MP_per_s": round(mp / (ms / 1e3), 2),
-                         "views_per_s": round(len(wl.views) / (ms / 1e3), 2)}
+        for name, groups in (("per_view", A.per_view(wl.scenes, wl.views)),
+                             ("batched_one_launch", A.one_launch(wl.scenes, wl.views))):
+            b = raster.Batch(ds, wl.views, wl.cfg, groups, device=dev)
+            b.size()
+            dls = b.dL_like(1e-6)
+            out[name] = entry(time_calls(lambda: b.step(dls), steps, warmup))
+            del b, dls
+            torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        plan = A.tune(wl.scenes, wl.views, wl.cfg, A.device_measure(ds, wl.views, wl.cfg, device=dev))
+        t_tune = time.perf_counter() - t0
+        from dataclasses import replace
+        cfg = replace(wl.cfg, tile_w=plan.tile[0], tile_h=plan.tile[1])
+        b = raster.Batch(ds, wl.views, cfg, plan.groups, device=dev)
+        b.size()
+        dls = b.dL_like(1e-6)
+        g = b.capture(dls)
+        out["batched"] = entry(time_calls(g.replay, steps, warmup))
+        out["batched"].update({"tile": f"{plan.tile[0]}x{plan.tile[1]}", "schedule": plan.schedule,
+                               "launches": len(plan.groups), "captured_graph": True})
+        out["autotune"] = {"seconds": round(t_tune, 1), "candidates_ms": plan.table}
         out["speedup_batched"] = round(out["per_view"]["ms_per_step"] / out["batched"]["ms_per_step"], 3)
         res[wl.name] = out
-        del batched, singles
+        del b, dls, g, ds
         torch.cuda.empty_cache()
     return res
 

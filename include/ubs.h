@@ -65,8 +65,12 @@ enum { UBS_ROT_QUAT = 0, UBS_ROT_SKEW1 = 1 };
 
 enum {
   UBS_FLAG_TIGHT_CUT = 1, /* cut each footprint at r_cut = 1-(a_min/o(q))^(1/beta_x) */
-  UBS_FLAG_COUNT_PAIRS = 2 /* diagnostic: ubs_render_fwd runs a variant that also counts,
-                              per pixel, the visited pairs with r < 1 (ubs_export 9) */
+  UBS_FLAG_COUNT_PAIRS = 2, /* diagnostic: ubs_render_fwd runs a variant that also counts,
+                               per pixel, the visited pairs with r < 1 (ubs_export 9) */
+  UBS_FLAG_ACCUMULATE_GRADS = 4 /* ubs_render_bwd / ubs_render_bwd_params ADD the parameter
+                                   gradients to the ubs_scene_grad buffers instead of
+                                   overwriting them: a scene rendered by several problems
+                                   (launches) gets the sum over all of its views */
 };
 
 /* One primitive set (Sec. 4.1-4.3).  Structure of arrays: every block below
@@ -101,7 +105,8 @@ typedef struct {
 } ubs_scene;
 
 /* Gradient buffers with the layout of ubs_scene (device pointers, 4-byte
- * aligned).  ubs_render_bwd OVERWRITES them (it does not accumulate). */
+ * aligned).  ubs_render_bwd OVERWRITES them, unless the problem's config has
+ * UBS_FLAG_ACCUMULATE_GRADS, in which case it adds to them. */
 typedef struct {
   float* mean_x;
   float* mean_q;
@@ -203,7 +208,8 @@ ubs_status ubs_render_bwd_blend(const ubs_problem* problem, void* workspace, siz
                                 const float* dL_dimage, cudaStream_t stream);
 
 /* G2 alone: chains the workspace's per-record screen gradients back to the
- * parameters of every scene (grads overwritten).  ubs_render_bwd is
+ * parameters of every scene (grads overwritten, or added to with
+ * UBS_FLAG_ACCUMULATE_GRADS).  ubs_render_bwd is
  * ubs_render_bwd_blend followed by ubs_render_bwd_params. */
 ubs_status ubs_render_bwd_params(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
                                  const ubs_scene_grad* grads, cudaStream_t stream);

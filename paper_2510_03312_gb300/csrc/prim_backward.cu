@@ -55,17 +55,20 @@ __global__ void __launch_bounds__(128) prim_backward_kernel(SceneDev sc, SceneGr
   PrimGrad<C> out;
   prim_backward_final<C>(in, vi, sc.rot_mode, acc, out);
   const int64_t P = sc.P;
-  for (int i = 0; i < 3; ++i) gr.mean_x[i * P + p] = out.mx[i];
+  // written, or added to the caller's running sum (UBS_FLAG_ACCUMULATE_GRADS)
+  const bool add = (cfg.flags & 4) != 0;
+  auto put = [&](float* dst, float v) { *dst = add ? *dst + v : v; };
+  for (int i = 0; i < 3; ++i) put(gr.mean_x + i * P + p, out.mx[i]);
   const int nr = sc.rot_mode == 0 ? 4 : 3;
-  for (int i = 0; i < nr; ++i) gr.rot[i * P + p] = out.rot[i];
-  for (int i = 0; i < 3; ++i) gr.scale_x[i * P + p] = out.s[i];
-  for (int i = 0; i < 1 + C; ++i) gr.b[i * P + p] = out.b[i];
-  gr.opacity[p] = out.o;
-  for (int i = 0; i < 3; ++i) gr.rgb[i * P + p] = out.rgb[i];
+  for (int i = 0; i < nr; ++i) put(gr.rot + i * P + p, out.rot[i]);
+  for (int i = 0; i < 3; ++i) put(gr.scale_x + i * P + p, out.s[i]);
+  for (int i = 0; i < 1 + C; ++i) put(gr.b + i * P + p, out.b[i]);
+  put(gr.opacity + p, out.o);
+  for (int i = 0; i < 3; ++i) put(gr.rgb + i * P + p, out.rgb[i]);
   if constexpr (C > 0) {
-    for (int i = 0; i < C; ++i) gr.mean_q[i * P + p] = out.mq[i];
-    for (int i = 0; i < 3 * C; ++i) gr.L_qx[i * P + p] = out.lqx[i];
-    for (int i = 0; i < C * (C + 1) / 2; ++i) gr.L_q[i * P + p] = out.lq[i];
+    for (int i = 0; i < C; ++i) put(gr.mean_q + i * P + p, out.mq[i]);
+    for (int i = 0; i < 3 * C; ++i) put(gr.L_qx + i * P + p, out.lqx[i]);
+    for (int i = 0; i < C * (C + 1) / 2; ++i) put(gr.L_q + i * P + p, out.lq[i]);
   }
 }
 

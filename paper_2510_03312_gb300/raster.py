@@ -7,6 +7,7 @@ part of the method.
 from __future__ import annotations
 
 import ctypes
+from dataclasses import replace
 
 import numpy as np
 import torch
@@ -88,7 +89,11 @@ class Rasterizer:
     shaped like the scene's params.
     """
 
-    def __init__(self, scenes, views, cfg: RasterConfig, capacity: int | None = None, device="cuda"):
+    def __init__(self, scenes, views, cfg: RasterConfig, capacity: int | None = None, device="cuda",
+                 grads=None, accumulate: bool = False):
+        """``grads``: optional gradient tensors (one per scene, shaped like its
+        params) to write into instead of fresh ones; with ``accumulate`` the
+        backward adds to them (UBS_FLAG_ACCUMULATE_GRADS)."""
         self.scenes = list(scenes)
         self.views = list(views)
         self.cfg = cfg
@@ -101,6 +106,8 @@ class Rasterizer:
         self.problem.views = self._view_structs
         self.problem.n_views = len(self.views)
         self.problem.cfg = config_struct(cfg)
+        if accumulate:
+            self.problem.cfg.flags |= U.UBS_FLAG_ACCUMULATE_GRADS
         self.R = sum(self.scenes[v.scene_id].P for v in self.views)
         self.pix_off = np.cumsum([0] + [v.width * v.height for v in self.views])
         self.n_pix = int(self.pix_off[-1])
@@ -108,7 +115,13 @@ class Rasterizer:
         self.ws_ptr, self.ws_bytes = None, 0
         self.set_capacity(capacity if capacity is not None else max(4 * self.R, 1 << 16))
         self.image = torch.empty(3 * self.n_pix, dtype=torch.float32, device=self.device)
-        self.grads = [torch.empty_like(s.params) for s in self.scenes]
+        if grads is None:
+            self.grads = [torch.empty_like(s.params) for s in self.scenes]
+        else:
+            self.grads = list(grads)
+            for g, s in zip(self.grads, self.scenes):
+                if g.shape != s.params.shape or g.dtype != torch.float32 or not g.is_contiguous():
+                    raise ValueError("each gradient tensor must be a contiguous float32 tensor shaped like params")
         self._grad_structs = (U.ubs_scene_grad * len(self.scenes))(
             *[s.grad_struct(g) for s, g in zip(self.scenes, self.grads)])
 
@@ -185,7 +198,19 @@ class Rasterizer:
     def backward(self, dL_dimage):
         return self.render_bwd(dL_dimage)
 
+    def capture(self, dL_dimage: torch.Tensor) -> torch.cuda.CUDAGraph:
+        """Captures one forward+backward step (preprocess, bin_sort,
+        render_fwd, render_bwd) into a CUDA graph; ``graph.replay()`` re-runs
+        it on the current tensors (params, dL_dimage, image, grads).  Size the
+        instance capacity first (``forward(check=True)``): a replay cannot
+        grow it, and an overflow shows up in ``status()``."""
+        return capture_steps([(self, dL_dimage)], self.device)
+
     # -- helpers
+    def n_tiles(self) -> int:
+        tw, th = int(self.cfg.tile_w), int(self.cfg.tile_h)
+        return sum(((v.width + tw - 1) // tw) * ((v.height + th - 1) // th) for v in self.views)
+
     def view_image(self, flat: torch.Tensor, v: int) -> torch.Tensor:
         w = self.views[v]
         o = int(self.pix_off[v]) * 3
@@ -201,6 +226,102 @@ class Rasterizer:
         st, _ = U.ubs_export(self.problem, self.ws_ptr, self.ws_bytes, what, out.data_ptr(), need, self.stream())
         self._check(st, "ubs_export")
         return out.view(dtype)
+
+
+def capture_steps(steps, device) -> torch.cuda.CUDAGraph:
+    """One CUDA graph of forward+backward over several (rasterizer, dL)
+    pairs, issued in order on one stream."""
+    def run():
+        for r, dL in steps:
+            r.forward(check=False)
+            r.backward(dL)
+
+    side = torch.cuda.Stream(device=device)
+    side.wait_stream(torch.cuda.current_stream(device))
+    with torch.cuda.stream(side):
+        run()  # warm-up outside the capture
+    torch.cuda.current_stream(device).wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run()
+    return g
+
+
+class Batch:
+    """A batch of render jobs over several scenes, run as the launches
+    (``groups``: lists of view indices) of a schedule.  Each launch is one
+    problem over the scenes its views use; every launch adds its gradients
+    into one buffer per scene, zeroed at the start of a step, so a scene's
+    gradient is the sum over all of its views whichever launch rendered
+    them.  Images are returned per view, in the original view order."""
+
+    def __init__(self, scenes, views, cfg: RasterConfig, groups, device="cuda"):
+        self.scenes = list(scenes)
+        self.views = list(views)
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.groups = [list(g) for g in groups]
+        seen = sorted(i for g in self.groups for i in g)
+        if seen != list(range(len(self.views))):
+            raise ValueError("groups must partition the views")
+        self.grads = [torch.zeros_like(s.params) for s in self.scenes]
+        self.rasterizers, self.slot = [], {}
+        for gi, g in enumerate(self.groups):
+            used = sorted({self.views[i].scene_id for i in g})
+            local = {s: k for k, s in enumerate(used)}
+            lv = [replace(self.views[i], scene_id=local[self.views[i].scene_id]) for i in g]
+            r = Rasterizer([self.scenes[s] for s in used], lv, cfg, device=self.device,
+                           grads=[self.grads[s] for s in used], accumulate=True)
+            self.rasterizers.append(r)
+            for k, i in enumerate(g):
+                self.slot[i] = (gi, k)
+
+    @property
+    def n_pix(self) -> int:
+        return sum(v.width * v.height for v in self.views)
+
+    def size(self):
+        """Runs every launch's forward once with the status check, growing
+        instance capacities where needed (synchronises)."""
+        for r in self.rasterizers:
+            r.forward(check=True)
+
+    def dL_like(self, fill=None):
+        """One dL/dimage tensor per launch (packed like its images)."""
+        return [torch.full_like(r.image, fill) if fill is not None else torch.zeros_like(r.image)
+                for r in self.rasterizers]
+
+    def zero_grads(self):
+        for g in self.grads:
+            g.zero_()
+
+    def step(self, dLs):
+        """Forward+backward of every launch (no synchronisation)."""
+        self.zero_grads()
+        for r, d in zip(self.rasterizers, dLs):
+            r.forward(check=False)
+            r.backward(d)
+        return self.grads
+
+    def capture(self, dLs) -> torch.cuda.CUDAGraph:
+        """The whole step (gradient zeroing and every launch) as one CUDA graph."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.step(dLs)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step(dLs)
+        return g
+
+    def image(self, i: int) -> torch.Tensor:
+        gi, k = self.slot[i]
+        r = self.rasterizers[gi]
+        return r.view_image(r.image, k)
+
+    def status(self):
+        return [r.status() for r in self.rasterizers]
 
 
 class UBSRasterize(torch.autograd.Function):

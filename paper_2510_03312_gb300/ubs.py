@@ -25,6 +25,7 @@ UBS_ROT_QUAT = 0
 UBS_ROT_SKEW1 = 1
 UBS_FLAG_TIGHT_CUT = 1
 UBS_FLAG_COUNT_PAIRS = 2
+UBS_FLAG_ACCUMULATE_GRADS = 4
 
 EXPORT_KEYS, EXPORT_TILES, EXPORT_RECT, EXPORT_RECORDS, EXPORT_INSTANCES = 0, 1, 2, 3, 4
 EXPORT_TILE_START, EXPORT_FINAL_T, EXPORT_LAST, EXPORT_SCREEN_GRAD, EXPORT_PAIRS = 5, 6, 7, 8, 9
