@@ -59,6 +59,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, dist, device):
+    """The maximum of a per-rank float over all ranks (x itself without a
+    process group): the job's elapsed time is its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, units_per_rank_step, total_ms):
+    """Whole-job throughput: the units every rank processed in ``steps``
+    steps over the (max-over-ranks) elapsed milliseconds."""
+    return world * steps * units_per_rank_step / (total_ms / 1e3)
+
+
 def workload(rank, P):
     from paper_2510_03312_gb300 import scenes as S
 
@@ -147,18 +165,28 @@ def source_sha(path):
 
 
 def traffic_record(kernel):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel source changed since it was captured."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    """DRAM bytes per launch of ``kernel`` from a committed ncu summary: a
+    line ``traffic: kernel=K source=F source_sha=S dram_bytes_per_launch=B``
+    in a profiles/*.md file.  None when no summary has one, or when the
+    kernel's source file changed since it was captured (sha mismatch)."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
         return None
-    d = json.load(open(p)).get(kernel)
-    if not d:
-        return None
-    src = os.path.join(ROOT, "paper_2510_03312_gb300", "csrc", d["source"])
-    if source_sha(src) != d["source_sha"]:
-        return None
-    return d["dram_bytes_per_launch"]
+    for name in sorted(os.listdir(d)):
+        if not name.endswith(".md"):
+            continue
+        for line in open(os.path.join(d, name)):
+            line = line.strip().strip("`")
+            if not line.startswith("traffic:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line[len("traffic:"):].split() if "=" in x)
+            if kv.get("kernel") != kernel:
+                continue
+            src = os.path.join(ROOT, "paper_2510_03312_gb300", "csrc", kv.get("source", ""))
+            if not os.path.exists(src) or source_sha(src) != kv.get("source_sha"):
+                return None
+            return int(kv["dram_bytes_per_launch"])
+    return None
 
 
 def kernels_per_step(r):
@@ -297,12 +325,9 @@ def bench_ours(args, rank, world, local):
     stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(5)] for e in all_evs])  # ms
     step_ms = stage.sum(1)
     total_ms = float(step_ms.sum())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     mp_per_view = wl.views[0].width * wl.views[0].height / 1e6
-    value = world * args.steps * mp_per_view / (total_ms / 1e3)
+    value = job_throughput(world, args.steps, mp_per_view, total_ms)
     ms_per_step = total_ms / args.steps
     # roofline of the dominant kernel
     stage_mean = stage.mean(0)
@@ -346,12 +371,9 @@ def bench_ours(args, rank, world, local):
         g_ms.append((e0, e1))
     torch.cuda.synchronize()
     g_total = float(sum(a.elapsed_time(b) for a, b in g_ms))
-    if dist:
-        t = torch.tensor([g_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        g_total = float(t.item())
+    g_total = max_over_ranks(g_total, dist, dev)
     graph_out = {"ms_per_step": round(g_total / args.steps, 4),
-                 "value": round(world * args.steps * mp_per_view / (g_total / 1e3), 2)}
+                 "value": round(job_throughput(world, args.steps, mp_per_view, g_total), 2)}
     del graph
     # end to end through the public API with host buffers
     e2e = bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view)
@@ -365,7 +387,7 @@ def bench_ours(args, rank, world, local):
                    "l2": "flushed (2x L2 buffer written) between timed steps",
                    "instances": int(st.instances), "visible_records": int(st.visible_records),
                    "pairs": pairs},
-        "views_per_sec": round(world * args.steps / (total_ms / 1e3), 2),
+        "views_per_sec": round(job_throughput(world, args.steps, 1, total_ms), 2),
         "stage_ms": {n: round(float(m), 4) for n, m in zip(names, stage_mean)},
         "roofline": roof,
         "roofline_steps": steps_roof,
@@ -416,13 +438,10 @@ def bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     bi = h_params.numel() * 4 + h_dL.numel() * 4
     bo = h_grad.numel() * 4 + h_img.numel() * 4
-    return {"value": round(world * args.steps * mp_per_view / (ms / 1e3), 2), "unit": "MP/s",
+    return {"value": round(job_throughput(world, args.steps, mp_per_view, ms), 2), "unit": "MP/s",
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": round(ms / args.steps, 4)}
 
 

@@ -225,7 +225,9 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     const uint32_t rel = base - start;
     for (int i = 0; i < cnt; i += 2) {
       if (__all_sync(kFull, done)) break;
-      // two entries evaluated independently, applied in order
+      // two entries evaluated independently, applied in order; the update is
+      // branch-free: a pair that is skipped (or stops the pixel) adds c * 0
+      // and keeps T, which leaves C and T exactly as they were
       const int j0 = list[i];
       const bool has1 = i + 1 < cnt;
       const int j1 = has1 ? list[i + 1] : j0;
@@ -233,36 +235,38 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
       eval_pair(fx, fy, s_p[j0], s_q[j0], cfg.amin, cfg.amax, e0);
       eval_pair(fx, fy, s_p[j1], s_q[j1], cfg.amin, cfg.amax, e1);
       if constexpr (COUNT) np += (!done && e0.r < 1.0f);
-      if (!done && e0.use) {
-        const float Tn = T * (1.0f - e0.alpha);
-        if (Tn < cfg.tmin) {
-          done = true;
-        } else {
-          const float w = e0.alpha * T;
-          const float4 q = s_q[j0];
-          const float2 c2 = s_s[j0];
-          C0 = fmaf(q.w, w, C0);
-          C1 = fmaf(c2.x, w, C1);
-          C2 = fmaf(c2.y, w, C2);
-          T = Tn;
-          last = rel + j0 + 1;
-        }
+      {
+        const bool u = !done && e0.use;
+        const float a = u ? e0.alpha : 0.0f;
+        const float Tn = T * (1.0f - a);
+        const bool term = u && Tn < cfg.tmin;
+        done = done || term;
+        const bool ok = u && !term;
+        const float w = ok ? a * T : 0.0f;
+        const float4 q = s_q[j0];
+        const float2 c2 = s_s[j0];
+        C0 = fmaf(q.w, w, C0);
+        C1 = fmaf(c2.x, w, C1);
+        C2 = fmaf(c2.y, w, C2);
+        T = ok ? Tn : T;
+        last = ok ? rel + j0 + 1 : last;
       }
       if constexpr (COUNT) np += (!done && has1 && e1.r < 1.0f);
-      if (!done && has1 && e1.use) {
-        const float Tn = T * (1.0f - e1.alpha);
-        if (Tn < cfg.tmin) {
-          done = true;
-        } else {
-          const float w = e1.alpha * T;
-          const float4 q = s_q[j1];
-          const float2 c2 = s_s[j1];
-          C0 = fmaf(q.w, w, C0);
-          C1 = fmaf(c2.x, w, C1);
-          C2 = fmaf(c2.y, w, C2);
-          T = Tn;
-          last = rel + j1 + 1;
-        }
+      {
+        const bool u = !done && has1 && e1.use;
+        const float a = u ? e1.alpha : 0.0f;
+        const float Tn = T * (1.0f - a);
+        const bool term = u && Tn < cfg.tmin;
+        done = done || term;
+        const bool ok = u && !term;
+        const float w = ok ? a * T : 0.0f;
+        const float4 q = s_q[j1];
+        const float2 c2 = s_s[j1];
+        C0 = fmaf(q.w, w, C0);
+        C1 = fmaf(c2.x, w, C1);
+        C2 = fmaf(c2.y, w, C2);
+        T = ok ? Tn : T;
+        last = ok ? rel + j1 + 1 : last;
       }
     }
   }

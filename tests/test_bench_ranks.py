@@ -1,0 +1,67 @@
+"""The multi-rank logic of bench.py, on CPU: the job time is the slowest
+rank's (max over a world_size-2 gloo group), the job value counts every
+rank's units, and every rank renders its own camera of the same scene
+(weak scaling, no collective on the data path)."""
+import os
+import socket
+
+import numpy as np
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 10.0 * (rank + 1) + 0.25
+        m = bench.max_over_ranks(local_ms, dist, "cpu")
+        v = bench.job_throughput(world, 4, 1.696, m)
+        dist.barrier()
+        q.put((rank, m, v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_value_over_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(2):
+        r, m, v = q.get(timeout=120)
+        res[r] = (m, v)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0] == res[1]
+    m, v = res[0]
+    assert m == 20.25
+    assert abs(v - 2 * 4 * 1.696 / 0.02025) < 1e-9
+
+
+def test_single_process_needs_no_group():
+    assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+    assert bench.job_throughput(1, 20, 1.696, 1000.0) == 20 * 1.696
+
+
+def test_each_rank_renders_its_own_camera_of_the_same_scene():
+    w0, w1 = bench.workload(0, 2000), bench.workload(1, 2000)
+    assert np.array_equal(w0.scenes[0].params, w1.scenes[0].params)
+    v0, v1 = w0.views[0], w1.views[0]
+    assert (v0.width, v0.height) == (v1.width, v1.height) == (1600, 1060)
+    assert not np.allclose(v0.R, v1.R)  # another camera on the same radius-8 sphere
