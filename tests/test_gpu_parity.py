@@ -179,6 +179,25 @@ def test_records_spanning_emission_blocks():
     check_grads(gpu, orc, ref, tiles=tiles)
 
 
+def test_very_long_tile_lists():
+    """24,000 primitives in a tiny cube: two tiles hold about 14,000
+    instances each (lists far longer than one blend batch or one sort
+    block)."""
+    sc = S.make_scene(65, 3, 24000, means="uniform", extent=0.04, scale_range=(0.01, 0.04))
+    R, t = S.look_at((0.0, 0.0, -3.0))
+    v = S.make_view(R, t, 96, 80)
+    cfg = S.RasterConfig()
+    orc = R64.Oracle([sc], [v], cfg)
+    counts = np.diff(orc.bins["ranges"], axis=1)[:, 0]
+    assert counts.max() > 8192
+    gpu = gpu_forward([sc], [v], cfg)
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    tiles = sorted(np.argsort(-counts)[:2].tolist())
+    _, _, ref = check_images(gpu, orc, recs=recs, tiles=tiles)
+    check_grads(gpu, orc, ref, tiles=tiles)
+
+
 def test_full_size_static_sampled():
     """The 1M-primitive 1600x1060 workload in the launch configuration the
     benchmark times: all records and instance lists bit-exact, images and
