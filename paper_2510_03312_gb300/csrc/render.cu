@@ -1,10 +1,10 @@
 // render.cu -- R1 (forward blend) and G1 (backward blend).
 //
-// One CTA per screen tile.  In the forward each warp owns an 8x4 pixel block
-// of the tile, one pixel per lane; in the backward an 8x8 block, two pixels
-// per lane (rows y and y + 4), which halves the per-entry warp reductions
-// there.  (Two pixels per lane made the forward slower: its per-pixel early
-// termination then diverges within a lane.)  The tile's front-to-back
+// Forward: one CTA per screen tile, each warp owning an 8x4 pixel block,
+// one pixel per lane.  Backward: one single-warp CTA per 8x8 block of a tile,
+// two pixels per lane (rows y and y + 4), which halves the per-entry warp
+// reductions.  (Two pixels per lane made the forward slower: its per-pixel
+// early termination then diverges within a lane.)  The tile's front-to-back
 // list (sorted record ids) is consumed in batches of up to 256 records: each
 // batch's 48-byte render records are staged in shared memory together with
 // a conservative screen box of each record's support (the ellipse
@@ -29,9 +29,8 @@
 // (mu', conic, log2 o(q), beta_x, rgb).  A lane first adds its two pixels'
 // contributions; the warp then sums its lanes with a transposed butterfly
 // (reduce-scatter: 12 shuffles for the 10 values, leaving each total in one
-// lane), the CTA's warps add per record in shared memory, and one vector
-// atomic add per (record, tile) flushes the sum -- never one global atomic
-// per pixel.
+// lane), and one vector atomic add per (record, block) flushes the sum --
+// never one global atomic per pixel.
 #include "kernels.cuh"
 
 namespace ubs {
@@ -39,10 +38,6 @@ namespace ubs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-// backward: pixels per lane (rows y and y + 4 of the warp's 8x8 block); four
-// per lane (8x16 blocks) measured 1.6x slower, at 97 registers
-constexpr int kBwdPPT = 2;
-
 __device__ __forceinline__ float lg2_approx(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -337,52 +332,44 @@ __device__ __forceinline__ int writer_of(int lane) {
 //   v7..9 = sum alpha T dL/dC.
 // With dr = -beta q:  d mu' = 2 beta [[a, b], [b, c]] (v0, v1),
 // d(a, b, c) = -beta (v2, 2 v3, v4), d log2 o = ln2 v5, d beta = ln2 v6.
-template <int TW, int TH, int kPPT>
-__global__ void __launch_bounds__(TW * TH / kPPT)
+//
+// One CTA of one warp per 8x8 block of a tile (two pixels a lane, rows y and
+// y + 4), with no block-wide barrier: warps of a tile finish independently
+// and free their slot at once.  The warp walks the tile's list back to front
+// from its block's last contributor in batches of 32 entries: each lane
+// stages one record, the batch is culled to the entries whose support meets
+// the block, those are processed, and each record the block used is flushed
+// by its lane with one vector atomic add per (record, block).
+template <int TW, int TH>
+__global__ void __launch_bounds__(32)
     render_bwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       const float* __restrict__ dLdimg, const float* __restrict__ Tfin,
                       const uint32_t* __restrict__ lastc, float4* __restrict__ g2d, const Header* hdr, uint32_t R) {
-  constexpr int NT = TW * TH / kPPT;  // threads
-  constexpr int BS = 256;             // records staged per batch
-  constexpr int NW = NT / 32;
-  __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
-  __shared__ float2 s_s[BS];
-  __shared__ float s_rc[BS];
-  __shared__ uint32_t s_rec[BS];
-  __shared__ float s_acc[10][BS + 1];  // +1: the 10 writer lanes hit 10 different banks
-  __shared__ int s_hit[BS];
-  __shared__ uint8_t s_list[NW][BS];
-  __shared__ int s_v;
-  __shared__ uint32_t s_max;
+  constexpr int WB = 32;             // entries per batch: one per lane
+  constexpr int BPT = TW * TH / 64;  // 8x8 blocks per tile
+  constexpr int WPR = TW / 8;        // blocks per row of the tile
+  __shared__ float4 s_p[WB], s_q[WB];
+  __shared__ float2 s_s[WB];
+  __shared__ uint32_t s_rec[WB];
+  __shared__ float s_acc[10][WB + 1];  // +1: the 10 writer lanes hit 10 different banks
+  __shared__ uint8_t s_list[WB];
   if (hdr->status != 0) return;
-  const uint32_t g = blockIdx.x;
-  if (threadIdx.x == 0) {
-    s_v = find_view(views, V, g);
-    s_max = 0;
-  }
-  for (int i = threadIdx.x; i < 10 * (BS + 1); i += NT) (&s_acc[0][0])[i] = 0.0f;
-  for (int i = threadIdx.x; i < BS; i += NT) s_hit[i] = 0;
-  __syncthreads();
-  const ViewDev& v = views[s_v];
+  const uint32_t g = blockIdx.x / BPT;
+  const int wb = blockIdx.x % BPT;
+  const int lane = threadIdx.x;
+  const ViewDev& v = views[find_view(views, V, g)];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
-  int lx, ly, bx, by;
-  pixel_of<TW, 4 * kPPT>(lx, ly, bx, by);
-  const float ox = (float)(tx * TW), oy = (float)(ty * TH);
-  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + (float)(4 * kPPT - 1);
-  const float lg2_amin = lg2_approx(cfg.amin);
-  uint8_t* list = s_list[threadIdx.x >> 5];
-  const uint32_t start = tstart[g];
-  const int lane = threadIdx.x & 31;
-  const int wslot = writer_of(lane);
+  const int bx = (wb % WPR) * 8, by = (wb / WPR) * 8;
+  const int lx = bx + (lane & 7), ly = by + (lane >> 3);
   const int x = tx * TW + lx;
   const float fx = (float)lx + 0.5f;
-  float fy[kPPT], T[kPPT], G0[kPPT], G1[kPPT], G2[kPPT], B0[kPPT], B1[kPPT], B2[kPPT];
-  uint32_t last[kPPT];
+  float fy[2], T[2], G0[2], G1[2], G2[2], B0[2], B1[2], B2[2];
+  uint32_t last[2];
   uint32_t mylast = 0;
 #pragma unroll
-  for (int k = 0; k < kPPT; ++k) {
+  for (int k = 0; k < 2; ++k) {
     const int y = ty * TH + ly + 4 * k;
     fy[k] = (float)(ly + 4 * k) + 0.5f;
     T[k] = 1.0f;
@@ -405,48 +392,52 @@ __global__ void __launch_bounds__(TW * TH / kPPT)
     mylast = max(mylast, last[k]);
   }
   const uint32_t wlast = __reduce_max_sync(kFull, mylast);
-  if (lane == 0 && wlast) atomicMax(&s_max, wlast);
-  __syncthreads();
-  const uint32_t nmax = s_max;
-  // batches from the back: entries [lo, hi) with hi = nmax, nmax - BS, ...
-  for (int hi = (int)nmax; hi > 0; hi -= BS) {
-    const int lo = hi - BS > 0 ? hi - BS : 0;
+  if (wlast == 0) return;
+  const float ox = (float)(tx * TW), oy = (float)(ty * TH);
+  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 7.0f;
+  const float lg2_amin = lg2_approx(cfg.amin);
+  const uint32_t start = tstart[g];
+  const int wslot = writer_of(lane);
+  for (int hi = (int)wlast; hi > 0; hi -= WB) {
+    const int lo = hi - WB > 0 ? hi - WB : 0;
     const int n = hi - lo;
-    __syncthreads();
-    for (int s = threadIdx.x; s < n; s += NT) {
-      const uint32_t r = min(ivals[start + lo + s], R - 1);  // ids are < R by construction
+    bool listed = false;
+    if (lane < n) {
+      const uint32_t r = min(ivals[start + lo + lane], R - 1);  // ids are < R by construction
       Staged st;
       float4 box;
-      stage_record(rec4, r, ox, oy, lg2_amin, st, box, s_rc[s]);
-      s_rec[s] = r;
-      s_p[s] = st.p;
-      s_q[s] = st.q;
-      s_s[s] = st.s;
-      s_bb[s] = box;
+      float rc;
+      stage_record(rec4, r, ox, oy, lg2_amin, st, box, rc);
+      s_rec[lane] = r;
+      s_p[lane] = st.p;
+      s_q[lane] = st.q;
+      s_s[lane] = st.s;
+      listed = box_hits(box, wx0, wx1, wy0, wy1) && ellipse_hits(st.p, st.q.x, rc, wx0, wx1, wy0, wy1);
     }
-    __syncthreads();
-    // entries past every lane's last contributor are not listed
-    const int nw = max(0, min(n, (int)wlast - lo));
-    const int cnt = warp_cull_list(s_bb, s_p, s_q, s_rc, nw, false, wx0, wx1, wy0, wy1, list);
-    for (int i = cnt - 1; i >= 0; --i) {
-      const int j = list[i];
+    const unsigned lm = __ballot_sync(kFull, listed);
+    if (listed) s_list[__popc(lm & ((1u << lane) - 1u))] = (uint8_t)lane;
+    __syncwarp();
+    unsigned touched = 0;  // entries the block used (warp-uniform)
+    for (int i = __popc(lm) - 1; i >= 0; --i) {
+      const int j = s_list[i];
       const float4 p = s_p[j], q = s_q[j];
       const float2 c2 = s_s[j];
-      PairEval e[kPPT];
-      bool use[kPPT], any = false;
+      PairEval e[2];
+      bool use[2], any = false;
 #pragma unroll
-      for (int k = 0; k < kPPT; ++k) {
+      for (int k = 0; k < 2; ++k) {
         eval_pair(fx, fy[k], p, q, cfg.amin, cfg.amax, e[k]);
         use[k] = e[k].use && (uint32_t)(lo + j) < last[k];  // pairs the forward composited
         any = any || use[k];
       }
       const unsigned hits = __ballot_sync(kFull, any);
       if (hits == 0) continue;  // no pixel of the block: T and B stay
+      touched |= 1u << j;
       float gv[10];
 #pragma unroll
       for (int m = 0; m < 10; ++m) gv[m] = 0.0f;
 #pragma unroll
-      for (int k = 0; k < kPPT; ++k) {
+      for (int k = 0; k < 2; ++k) {
         // branch-free: a pair the forward skipped contributes zero and leaves T, B
         const float a = use[k] ? e[k].alpha : 0.0f;
         T[k] = __fdividef(T[k], 1.0f - a);  // transmittance before this record
@@ -473,30 +464,26 @@ __global__ void __launch_bounds__(TW * TH / kPPT)
       if (__popc(hits) == 1) {  // one lane: its values are the totals
         if (any) {
 #pragma unroll
-          for (int m = 0; m < 10; ++m) atomicAdd(&s_acc[m][j], gv[m]);
-          s_hit[j] = 1;
+          for (int m = 0; m < 10; ++m) s_acc[m][j] = gv[m];
         }
       } else {
         const float tot = warp_reduce10(gv, lane);
-        if (wslot >= 0) atomicAdd(&s_acc[wslot][j], tot);
-        if (lane == 0) s_hit[j] = 1;
+        if (wslot >= 0) s_acc[wslot][j] = tot;
       }
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += NT) {
-      if (!s_hit[j]) continue;
-      const float4 p = s_p[j], q = s_q[j];
+    __syncwarp();
+    if ((touched >> lane) & 1u) {
+      const float4 p = s_p[lane], q = s_q[lane];
       const float a = p.z, b = 0.5f * p.w, c = q.x, beta = q.z;
-      const float v0 = s_acc[0][j], v1 = s_acc[1][j];
-      float4* dst = g2d + 3 * (size_t)s_rec[j];
+      const float v0 = s_acc[0][lane], v1 = s_acc[1][lane];
+      float4* dst = g2d + 3 * (size_t)s_rec[lane];
       atomicAdd(dst, make_float4(2.0f * beta * (a * v0 + b * v1), 2.0f * beta * (b * v0 + c * v1),
-                                 -beta * s_acc[2][j], -2.0f * beta * s_acc[3][j]));
-      atomicAdd(dst + 1, make_float4(-beta * s_acc[4][j], kLn2f * s_acc[5][j], kLn2f * s_acc[6][j], s_acc[7][j]));
-      atomicAdd((float2*)(dst + 2), make_float2(s_acc[8][j], s_acc[9][j]));
-#pragma unroll
-      for (int m = 0; m < 10; ++m) s_acc[m][j] = 0.0f;
-      s_hit[j] = 0;
+                                 -beta * s_acc[2][lane], -2.0f * beta * s_acc[3][lane]));
+      atomicAdd(dst + 1, make_float4(-beta * s_acc[4][lane], kLn2f * s_acc[5][lane], kLn2f * s_acc[6][lane],
+                                     s_acc[7][lane]));
+      atomicAdd((float2*)(dst + 2), make_float2(s_acc[8][lane], s_acc[9][lane]));
     }
+    __syncwarp();
   }
 }
 
@@ -521,7 +508,7 @@ cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cu
 
 template <int TW, int TH>
 cudaError_t bwd_t(const Layout& L, const CfgDev& cfg, char* ws, const float* dL, cudaStream_t st) {
-  render_bwd_kernel<TW, TH, kBwdPPT><<<L.NT, TW * TH / kBwdPPT, 0, st>>>(
+  render_bwd_kernel<TW, TH><<<L.NT * (TW * TH / 64), 32, 0, st>>>(
       (const ViewDev*)(ws + L.views), L.V, cfg, (const uint32_t*)(ws + L.tstart), sorted_instances(L, ws),
       (const float4*)(ws + L.rec4), dL, (const float*)(ws + L.Tfin), (const uint32_t*)(ws + L.last),
       (float4*)(ws + L.g2d), (const Header*)(ws + L.header), L.R > 0 ? L.R : 1);
