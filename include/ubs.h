@@ -224,7 +224,8 @@ ubs_status ubs_read_status(const ubs_problem* problem, void* workspace, size_t w
  * x1|y1<<16), 3 = render records [R] x 12 f32, 4 = sorted instance records
  * [instances] u32, 5 = tile starts [tiles + 1] u32, 6 = final T [pixels]
  * f32, 7 = last contributor [pixels] u32, 8 = per-record screen gradients
- * [R] x 12 f32, 9 = visited pairs with r < 1 [pixels] u32 (written by the
+ * [R] x 12 f32 (3 and 8 are defined for the visible records, those with
+ * tiles_touched > 0), 9 = visited pairs with r < 1 [pixels] u32 (written by the
  * UBS_FLAG_COUNT_PAIRS variant of ubs_render_fwd).  `dst` is device memory of at least `dst_bytes`; returns the
  * bytes needed in *bytes_needed. */
 ubs_status ubs_export(const ubs_problem* problem, void* workspace, size_t workspace_bytes,

@@ -7,6 +7,30 @@
 
 namespace ubs {
 
+// Programmatic dependent launch (sm_90 and later): a kernel started with
+// launch_dependent may be scheduled while the previous kernel on the stream
+// drains.  It must call wait_prior_grid() before its first access to memory
+// written by earlier work: griddepcontrol.wait returns once the previous
+// grid has completed and its writes are visible (and at once for a kernel
+// launched without the attribute).  Every kernel waiting first keeps the
+// ordering transitive.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... Params, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // the views that render one scene, by index into the view table
 struct ViewList {
   int32_t n;

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList v
                                                          CfgDev cfg, float4* __restrict__ rec4,
                                                          uint32_t* __restrict__ key, uint32_t* __restrict__ tiles,
                                                          uint2* __restrict__ rect, uint32_t* __restrict__ vis_count) {
+  wait_prior_grid();
   extern __shared__ ViewDev s_views[];
   for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
   __syncthreads();
@@ -81,10 +82,10 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
   uint2* rect = (uint2*)(ws + L.rect);
   uint32_t* vis = (uint32_t*)(ws + L.vis_count);
   switch (sc.N) {
-    case 3: preprocess_kernel<0><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
-    case 4: preprocess_kernel<1><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
-    case 6: preprocess_kernel<3><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
-    case 7: preprocess_kernel<4><<<blocks, threads, smem, st>>>(sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 3: launch_dependent(preprocess_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 4: launch_dependent(preprocess_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 6: launch_dependent(preprocess_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 7: launch_dependent(preprocess_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(128, C == 0 ? 6 : 1) prim_backward_kernel(Scen
                                                             const ViewDev* __restrict__ views, CfgDev cfg,
                                                             const uint32_t* __restrict__ tiles,
                                                             const float4* __restrict__ g2d) {
+  wait_prior_grid();
   extern __shared__ ViewDev s_views[];
   for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
   __syncthreads();
@@ -86,10 +87,10 @@ cudaError_t launch_prim_backward(const SceneDev& sc, const SceneGradDev& g, cons
   const uint32_t* tiles = (const uint32_t*)(ws + L.tiles);
   const float4* g2d = (const float4*)(ws + L.g2d);
   switch (sc.N) {
-    case 3: prim_backward_kernel<0><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
-    case 4: prim_backward_kernel<1><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
-    case 6: prim_backward_kernel<3><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
-    case 7: prim_backward_kernel<4><<<blocks, threads, smem, st>>>(sc, g, vl, views, cfg, tiles, g2d); break;
+    case 3: launch_dependent(prim_backward_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, g, vl, views, cfg, tiles, g2d); break;
+    case 4: launch_dependent(prim_backward_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, g, vl, views, cfg, tiles, g2d); break;
+    case 6: launch_dependent(prim_backward_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, g, vl, views, cfg, tiles, g2d); break;
+    case 7: launch_dependent(prim_backward_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, g, vl, views, cfg, tiles, g2d); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       float* __restrict__ image, float* __restrict__ Tfin, uint32_t* __restrict__ lastc,
                       const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs) {
+  wait_prior_grid();
   constexpr int B = TW * TH;
   constexpr int BS = B < 256 ? B : 256;  // records staged per batch
   constexpr int NW = B / 32;
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(32)
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       const float* __restrict__ dLdimg, const float* __restrict__ Tfin,
                       const uint32_t* __restrict__ lastc, float4* __restrict__ g2d, const Header* hdr, uint32_t R) {
+  wait_prior_grid();
   constexpr int WB = 32;             // entries per batch: one per lane
   constexpr int BPT = TW * TH / 64;  // 8x8 blocks per tile
   constexpr int WPR = TW / 8;        // blocks per row of the tile
@@ -487,6 +489,20 @@ __global__ void __launch_bounds__(32)
   }
 }
 
+// Zeroes the per-record gradient accumulators of the visible records (those
+// with tiles): the only ones the backward blend adds to and the parameter
+// backward reads.
+__global__ void __launch_bounds__(256) zero_visible_grads_kernel(const uint32_t* __restrict__ tiles, uint32_t R,
+                                                                 float4* __restrict__ g2d) {
+  wait_prior_grid();
+  const uint32_t r = blockIdx.x * 256 + threadIdx.x;
+  if (r >= R || tiles[r] == 0) return;
+  const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  g2d[3 * (size_t)r] = z;
+  g2d[3 * (size_t)r + 1] = z;
+  g2d[3 * (size_t)r + 2] = z;
+}
+
 template <int TW, int TH>
 cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cudaStream_t st) {
   const ViewDev* views = (const ViewDev*)(ws + L.views);
@@ -498,17 +514,17 @@ cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cu
   const uint32_t R = L.R > 0 ? L.R : 1;
   constexpr int NT = TW * TH;
   if (cfg.flags & 2)  // diagnostic variant: also count visited pairs with r < 1 per pixel
-    render_fwd_kernel<TW, TH, true><<<L.NT, NT, 0, st>>>(views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
+    launch_dependent(render_fwd_kernel<TW, TH, true>, dim3(L.NT), dim3(NT), 0, st, views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
                                                        image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs));
   else
-    render_fwd_kernel<TW, TH, false><<<L.NT, NT, 0, st>>>(views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
+    launch_dependent(render_fwd_kernel<TW, TH, false>, dim3(L.NT), dim3(NT), 0, st, views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
                                                         image, Tfin, last, hdr, R, nullptr);
   return cudaGetLastError();
 }
 
 template <int TW, int TH>
 cudaError_t bwd_t(const Layout& L, const CfgDev& cfg, char* ws, const float* dL, cudaStream_t st) {
-  render_bwd_kernel<TW, TH><<<L.NT * (TW * TH / 64), 32, 0, st>>>(
+  launch_dependent(render_bwd_kernel<TW, TH>, dim3(L.NT * (TW * TH / 64)), dim3(32), 0, st, 
       (const ViewDev*)(ws + L.views), L.V, cfg, (const uint32_t*)(ws + L.tstart), sorted_instances(L, ws),
       (const float4*)(ws + L.rec4), dL, (const float*)(ws + L.Tfin), (const uint32_t*)(ws + L.last),
       (float4*)(ws + L.g2d), (const Header*)(ws + L.header), L.R > 0 ? L.R : 1);
@@ -528,7 +544,8 @@ cudaError_t launch_render_fwd(const Layout& L, const CfgDev& cfg, char* ws, floa
 
 cudaError_t launch_render_bwd(const Layout& L, const CfgDev& cfg, char* ws, const float* dL, cudaStream_t st) {
   if (L.NT == 0 || L.R == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(ws + L.g2d, 0, (size_t)L.R * kGradFloats * sizeof(float), st);
+  cudaError_t e = launch_dependent(zero_visible_grads_kernel, dim3((L.R + 255) / 256), dim3(256), 0, st,
+                                   (const uint32_t*)(ws + L.tiles), L.R, (float4*)(ws + L.g2d));
   if (e != cudaSuccess) return e;
   if (cfg.tw == 16 && cfg.th == 16) return bwd_t<16, 16>(L, cfg, ws, dL, st);
   if (cfg.tw == 8 && cfg.th == 8) return bwd_t<8, 8>(L, cfg, ws, dL, st);

@@ -90,6 +90,7 @@ constexpr int kScT = 256, kScI = 4;
 // non-null).
 __global__ void __launch_bounds__(kScT) col_scan_kernel(const uint32_t* in, uint32_t* out, uint32_t rows,
                                                         uint32_t cols, uint32_t* totals) {
+  wait_prior_grid();
   __shared__ uint32_t s_w[kScT / 32 + 1];
   const uint32_t c = blockIdx.x;
   uint32_t carry = 0;
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restri
                                                         const uint32_t* __restrict__ vis_prefix,
                                                         uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
                                                         uint32_t* __restrict__ hist0, Header* hdr) {
+  wait_prior_grid();
   __shared__ uint32_t s_w[kCmpT / 32 + 1];
   const uint32_t t = blockIdx.x;
   const uint32_t excl = vis_prefix[t];
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
                                                          uint32_t cap, int shift, const uint32_t* __restrict__ ghist,
                                                          const uint32_t* __restrict__ hprefix, uint32_t* hnext,
                                                          uint32_t* icount, const uint32_t* __restrict__ tiles_touched) {
+  wait_prior_grid();
   constexpr int kOsI = TILE / kOsT;
   __shared__ uint32_t s_keys[TILE];
   __shared__ uint32_t s_vals[TILE];
@@ -295,6 +298,7 @@ __global__ void __launch_bounds__(kEmT) emit_offsets_kernel(const uint32_t* __re
                                                             const uint32_t* __restrict__ tiles,
                                                             const uint32_t* __restrict__ icount_prefix,
                                                             uint32_t* __restrict__ ioff, uint32_t cap, Header* hdr) {
+  wait_prior_grid();
   __shared__ uint32_t s_w[kEmT / 32 + 1];
   const uint32_t n = (uint32_t)hdr->n_visible;
   const uint32_t t = blockIdx.x;
@@ -338,6 +342,7 @@ __global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restr
                                                          const ViewDev* __restrict__ views, int V, uint32_t cap,
                                                          uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
                                                          uint32_t* __restrict__ hist0, const Header* hdr) {
+  wait_prior_grid();
   __shared__ uint32_t s_off[kIsTile + 1];
   __shared__ uint32_t s_h[256];
   __shared__ uint32_t s_recoff[kMaxViews], s_tileoff[kMaxViews], s_tilesx[kMaxViews];
@@ -434,6 +439,7 @@ __global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restr
 // first position whose key is >= g, and tstart[NT] = n.
 __global__ void ranges_kernel(const uint32_t* __restrict__ skeys, const uint64_t* n_ptr, uint32_t cap, uint32_t NT,
                               uint32_t* __restrict__ tstart) {
+  wait_prior_grid();
   const uint64_t n64 = *n_ptr;
   const uint32_t n = (uint32_t)(n64 < cap ? n64 : cap);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
@@ -467,9 +473,9 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* cvA = (uint32_t*)(ws + L.cvA);
   uint32_t* ckB = (uint32_t*)(ws + L.ckB);
   uint32_t* cvB = (uint32_t*)(ws + L.cvB);
-  col_scan_kernel<<<1, kScT, 0, st>>>(vis, vis_prefix, L.n_cmp_tiles, 1, nullptr);
+  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, vis, vis_prefix, L.n_cmp_tiles, 1, nullptr);
   const size_t hd_stride = (size_t)L.n_dsort_tiles * 256;
-  compact_kernel<<<L.n_cmp_tiles, kCmpT, 0, st>>>(tiles, (const uint32_t*)(ws + L.key), L.R, vis_prefix, ckA, cvA,
+  launch_dependent(compact_kernel, dim3(L.n_cmp_tiles), dim3(kCmpT), 0, st, tiles, (const uint32_t*)(ws + L.key), L.R, vis_prefix, ckA, cvA,
                                                   hd, hdr);
   // depth sort: 4 passes A->B->A->B->A; the last one counts instances per
   // emission block
@@ -477,8 +483,8 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
     const bool even = (p & 1) == 0;
     uint32_t* hp = hd + p * hd_stride;
     const bool last = p == 3;
-    col_scan_kernel<<<256, kScT, 0, st>>>(hp, hp, L.n_dsort_tiles, 256, ghist + 256 * p);
-    downsweep_kernel<kDsTile><<<L.n_dsort_tiles, kOsT, 0, st>>>(even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
+    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_dsort_tiles, 256, ghist + 256 * p);
+    launch_dependent(downsweep_kernel<kDsTile>, dim3(L.n_dsort_tiles), dim3(kOsT), 0, st, even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
                                                        even ? cvB : cvA, &hdr->n_visible, L.R, 8 * p, ghist + 256 * p,
                                                        hp, last ? nullptr : hp + hd_stride, last ? icount : nullptr,
                                                        tiles);
@@ -488,10 +494,10 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* ikB = (uint32_t*)(ws + L.ikB);
   uint32_t* ivB = (uint32_t*)(ws + L.ivB);
   const ViewDev* views = (const ViewDev*)(ws + L.views);
-  col_scan_kernel<<<1, kScT, 0, st>>>(icount, icount, L.n_emit_tiles, 1, nullptr);
+  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, icount, icount, L.n_emit_tiles, 1, nullptr);
   uint32_t* ioff = (uint32_t*)(ws + L.ioff);
-  emit_offsets_kernel<<<L.n_emit_tiles, kEmT, 0, st>>>(cvA, tiles, icount, ioff, L.cap, hdr);
-  emit_fill_kernel<<<L.n_isort_tiles, kFlT, 0, st>>>(cvA, ioff, (const uint2*)(ws + L.rect), views, L.V, L.cap,
+  launch_dependent(emit_offsets_kernel, dim3(L.n_emit_tiles), dim3(kEmT), 0, st, cvA, tiles, icount, ioff, L.cap, hdr);
+  launch_dependent(emit_fill_kernel, dim3(L.n_isort_tiles), dim3(kFlT), 0, st, cvA, ioff, (const uint2*)(ws + L.rect), views, L.V, L.cap,
                                                      ikA, ivA, L.tile_passes > 0 ? hi : nullptr, hdr);
   uint32_t* gh_tile = ghist + 4 * 256;
   const size_t hi_stride = (size_t)L.n_isort_tiles * 256;
@@ -499,14 +505,14 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
     const bool even = (p & 1) == 0;
     uint32_t* hp = hi + p * hi_stride;
     const bool last = p == L.tile_passes - 1;
-    col_scan_kernel<<<256, kScT, 0, st>>>(hp, hp, L.n_isort_tiles, 256, gh_tile + 256 * p);
-    downsweep_kernel<kIsTile><<<L.n_isort_tiles, kOsT, 0, st>>>(even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
+    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_isort_tiles, 256, gh_tile + 256 * p);
+    launch_dependent(downsweep_kernel<kIsTile>, dim3(L.n_isort_tiles), dim3(kOsT), 0, st, even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
                                                        even ? ivB : ivA, &hdr->n_inst, L.cap, 8 * p,
                                                        gh_tile + 256 * p, hp, last ? nullptr : hp + hi_stride,
                                                        nullptr, nullptr);
   }
   const uint32_t* skeys = (const uint32_t*)(ws + ((L.tile_passes & 1) ? L.ikB : L.ikA));
-  ranges_kernel<<<592, 256, 0, st>>>(skeys, &hdr->n_inst, L.cap, L.NT, (uint32_t*)(ws + L.tstart));
+  launch_dependent(ranges_kernel, dim3(592), dim3(256), 0, st, skeys, &hdr->n_inst, L.cap, L.NT, (uint32_t*)(ws + L.tstart));
   return cudaGetLastError();
 }
 
