@@ -201,7 +201,9 @@ def kernels_per_step(r):
     # scan, compact, 4 depth passes (scan + downsweep), scan, emission offsets
     # and fill, tile-key passes (scan + downsweep), ranges
     sort = 2 + 4 * 2 + 3 + 2 * tile_passes + 1
-    return pre + sort + 1 + 1 + S
+    # forward blend; zeroing of the visible records' gradient sums, backward
+    # blend; parameter backward per scene
+    return pre + sort + 1 + 2 + S
 
 
 def step_rooflines(stage_ms, names, params_bytes, R, instances, NT, pairs, pk, n_sm):
