@@ -402,6 +402,7 @@ def bench_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_batched and world == 1:
         out["batched"] = bench_batched(dev)
+        out["forward_only"] = bench_small_forward(dev)
     if dist:
         dist.destroy_process_group()
     return out
@@ -496,6 +497,36 @@ def time_calls(fn, steps, warmup):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def bench_small_forward(dev, steps=200, warmup=20):
+    """The static N=3 4,096-primitive 128x128 view, forward only (preprocess
+    -> bin_sort -> render_fwd), eagerly and replayed as one captured graph."""
+    import torch
+
+    from paper_2510_03312_gb300 import raster
+    from paper_2510_03312_gb300 import scenes as S
+
+    wl = S.workload_static_small()
+    ds = raster.DeviceScene.from_scene(wl.scenes[0], device=dev)
+    r = raster.Rasterizer([ds], wl.views, wl.cfg, device=dev)
+    r.forward(check=True)
+    mp = wl.views[0].width * wl.views[0].height / 1e6
+    eager = time_calls(lambda: r.forward(check=False), steps, warmup)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        r.forward(check=False)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        r.forward(check=False)
+    graph = time_calls(g.replay, steps, warmup)
+    out = {}
+    for name, ms in (("eager", eager), ("graph", graph)):
+        out[name] = {"ms_per_step": round(ms, 5), "MP_per_s": round(mp / (ms / 1e3), 2),
+                     "views_per_s": round(1 / (ms / 1e3), 1)}
+    return {wl.name: out}
 
 
 def bench_batched(dev, steps=5, warmup=2):
