@@ -87,12 +87,19 @@ constexpr int kScT = 256, kScI = 4;
 
 // Exclusive scan down each column of a row-major [rows][cols] matrix (out
 // may equal in); one block per column; the column sums go to totals (if
-// non-null).
+// non-null).  With n_ptr, only the first ceil(min(*n_ptr, cap) / per_row)
+// rows are scanned: the rows that can hold counts of n items.
 __global__ void __launch_bounds__(kScT) col_scan_kernel(const uint32_t* in, uint32_t* out, uint32_t rows,
-                                                        uint32_t cols, uint32_t* totals) {
+                                                        uint32_t cols, uint32_t* totals, const uint64_t* n_ptr,
+                                                        uint32_t cap, uint32_t per_row) {
   wait_prior_grid();
   __shared__ uint32_t s_w[kScT / 32 + 1];
   const uint32_t c = blockIdx.x;
+  if (n_ptr) {
+    const uint64_t n = *n_ptr < cap ? *n_ptr : cap;
+    const uint64_t used = (n + per_row - 1) / per_row;
+    if (used < rows) rows = (uint32_t)used;
+  }
   uint32_t carry = 0;
   for (uint32_t r0 = 0; r0 < rows; r0 += kScT * kScI) {
     uint32_t v[kScI], sum = 0;
@@ -201,88 +208,91 @@ __global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restr
   __shared__ uint32_t s_w[kOsT / 32 + 1];
   const uint64_t n64 = *n_ptr;
   const uint32_t n = (uint32_t)(n64 < cap ? n64 : cap);
-  const uint32_t t = blockIdx.x;
-  const uint32_t tile_base = t * TILE;
-  if (tile_base >= n) return;
-  for (int i = threadIdx.x; i < kOsW * 256; i += kOsT) (&s_hist[0][0])[i] = 0;
-  __syncthreads();
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint32_t wbase = tile_base + warp * (kOsI * 32);
-  uint32_t k[kOsI], v[kOsI], rank[kOsI];
+  // grid-stride over the pass's tiles (the grid is sized by the capacity,
+  // the work by the count found on the device)
+  for (uint32_t t = blockIdx.x; (uint64_t)t * TILE < n; t += gridDim.x) {
+    __syncthreads();  // the shared arrays of the previous tile are free
+    const uint32_t tile_base = t * TILE;
+    for (int i = threadIdx.x; i < kOsW * 256; i += kOsT) (&s_hist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t wbase = tile_base + warp * (kOsI * 32);
+    uint32_t k[kOsI], v[kOsI], rank[kOsI];
 #pragma unroll
-  for (int i = 0; i < kOsI; ++i) {
-    const uint32_t idx = wbase + i * 32 + lane;
-    const bool ok = idx < n;
-    k[i] = ok ? kin[idx] : 0u;
-    v[i] = ok ? vin[idx] : 0u;
-  }
-#pragma unroll
-  for (int i = 0; i < kOsI; ++i) {
-    const uint32_t idx = wbase + i * 32 + lane;
-    const bool ok = idx < n;
-    const uint32_t d = ok ? (k[i] >> shift) & 255u : 0x100u;
-    const uint32_t peers = peer_mask(d);
-    uint32_t cnt = 0;
-    if (d < 256) cnt = s_hist[warp][d];
-    __syncwarp();
-    rank[i] = ok ? cnt + __popc(peers & lt_mask) : 0xffffffffu;
-    if (d < 256 && lane == (uint32_t)(__ffs(peers) - 1)) s_hist[warp][d] = cnt + __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  const uint32_t d = threadIdx.x;  // one digit per thread
-  uint32_t acc = 0;
-#pragma unroll
-  for (int w = 0; w < kOsW; ++w) {
-    const uint32_t c = s_hist[w][d];
-    s_hist[w][d] = acc;
-    acc += c;
-  }
-  uint32_t gtot;
-  const uint32_t gbase = block_excl_scan<kOsT>(ghist[d], gtot, s_w);
-  uint32_t btot;
-  const uint32_t boff = block_excl_scan<kOsT>(acc, btot, s_w);
-  s_boff[d] = boff;
-  s_goff[d] = gbase + hprefix[(size_t)t * 256 + d] - boff;
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < kOsI; ++i) {
-    if (rank[i] != 0xffffffffu) {
-      const uint32_t dd = (k[i] >> shift) & 255u;
-      const uint32_t pos = s_boff[dd] + s_hist[warp][dd] + rank[i];
-      s_keys[pos] = k[i];
-      s_vals[pos] = v[i];
+    for (int i = 0; i < kOsI; ++i) {
+      const uint32_t idx = wbase + i * 32 + lane;
+      const bool ok = idx < n;
+      k[i] = ok ? kin[idx] : 0u;
+      v[i] = ok ? vin[idx] : 0u;
     }
-  }
-  __syncthreads();
-  const uint32_t cnt_tile = (n - tile_base) < (uint32_t)TILE ? (n - tile_base) : (uint32_t)TILE;
-#pragma unroll 4
-  for (int it = 0; it < kOsI; ++it) {
-    const uint32_t j = it * kOsT + threadIdx.x;
-    bool valid = j < cnt_tile;
-    uint32_t key = 0, val = 0, g = 0;
-    if (valid) {
-      key = s_keys[j];
-      val = s_vals[j];
-      g = s_goff[(key >> shift) & 255u] + j;
-      valid = g < n;  // holds by construction (consistent digit counts)
-      if (valid) {
-        kout[g] = key;
-        vout[g] = val;
+#pragma unroll
+    for (int i = 0; i < kOsI; ++i) {
+      const uint32_t idx = wbase + i * 32 + lane;
+      const bool ok = idx < n;
+      const uint32_t d = ok ? (k[i] >> shift) & 255u : 0x100u;
+      const uint32_t peers = peer_mask(d);
+      uint32_t cnt = 0;
+      if (d < 256) cnt = s_hist[warp][d];
+      __syncwarp();
+      rank[i] = ok ? cnt + __popc(peers & lt_mask) : 0xffffffffu;
+      if (d < 256 && lane == (uint32_t)(__ffs(peers) - 1)) s_hist[warp][d] = cnt + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    const uint32_t d = threadIdx.x;  // one digit per thread
+    uint32_t acc = 0;
+#pragma unroll
+    for (int w = 0; w < kOsW; ++w) {
+      const uint32_t c = s_hist[w][d];
+      s_hist[w][d] = acc;
+      acc += c;
+    }
+    uint32_t gtot;
+    const uint32_t gbase = block_excl_scan<kOsT>(ghist[d], gtot, s_w);
+    uint32_t btot;
+    const uint32_t boff = block_excl_scan<kOsT>(acc, btot, s_w);
+    s_boff[d] = boff;
+    s_goff[d] = gbase + hprefix[(size_t)t * 256 + d] - boff;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kOsI; ++i) {
+      if (rank[i] != 0xffffffffu) {
+        const uint32_t dd = (k[i] >> shift) & 255u;
+        const uint32_t pos = s_boff[dd] + s_hist[warp][dd] + rank[i];
+        s_keys[pos] = k[i];
+        s_vals[pos] = v[i];
       }
     }
-    if (hnext) {
-      const uint32_t grp = valid ? ((g / TILE) << 8) | ((key >> (shift + 8)) & 255u) : 0xffffffffu;
-      const uint32_t peers = __match_any_sync(kFull, grp);
-      if (valid && lane == (uint32_t)(__ffs(peers) - 1))
-        atomicAdd(hnext + (size_t)(grp >> 8) * 256 + (grp & 255u), (uint32_t)__popc(peers));
-    }
-    if (icount) {
-      const uint32_t grp = valid ? g / kEmTile : 0xffffffffu;
-      const uint32_t peers = __match_any_sync(kFull, grp);
-      const uint32_t sum = __reduce_add_sync(peers, valid ? tiles_touched[val] : 0u);
-      if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(icount + grp, sum);
+    __syncthreads();
+    const uint32_t cnt_tile = (n - tile_base) < (uint32_t)TILE ? (n - tile_base) : (uint32_t)TILE;
+#pragma unroll 4
+    for (int it = 0; it < kOsI; ++it) {
+      const uint32_t j = it * kOsT + threadIdx.x;
+      bool valid = j < cnt_tile;
+      uint32_t key = 0, val = 0, g = 0;
+      if (valid) {
+        key = s_keys[j];
+        val = s_vals[j];
+        g = s_goff[(key >> shift) & 255u] + j;
+        valid = g < n;  // holds by construction (consistent digit counts)
+        if (valid) {
+          kout[g] = key;
+          vout[g] = val;
+        }
+      }
+      if (hnext) {
+        const uint32_t grp = valid ? ((g / TILE) << 8) | ((key >> (shift + 8)) & 255u) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(kFull, grp);
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1))
+          atomicAdd(hnext + (size_t)(grp >> 8) * 256 + (grp & 255u), (uint32_t)__popc(peers));
+      }
+      if (icount) {
+        const uint32_t grp = valid ? g / kEmTile : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(kFull, grp);
+        const uint32_t sum = __reduce_add_sync(peers, valid ? tiles_touched[val] : 0u);
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(icount + grp, sum);
+      }
     }
   }
 }
@@ -301,27 +311,27 @@ __global__ void __launch_bounds__(kEmT) emit_offsets_kernel(const uint32_t* __re
   wait_prior_grid();
   __shared__ uint32_t s_w[kEmT / 32 + 1];
   const uint32_t n = (uint32_t)hdr->n_visible;
-  const uint32_t t = blockIdx.x;
   const uint32_t n_blocks = (n + kEmTile - 1) / kEmTile;
-  if (t >= n_blocks) return;
-  const uint32_t base = t * kEmTile + threadIdx.x * kEmI;
-  uint32_t c[kEmI], sum = 0;
+  for (uint32_t t = blockIdx.x; t < n_blocks; t += gridDim.x) {
+    const uint32_t base = t * kEmTile + threadIdx.x * kEmI;
+    uint32_t c[kEmI], sum = 0;
 #pragma unroll
-  for (int i = 0; i < kEmI; ++i) {
-    c[i] = base + i < n ? tiles[srec[base + i]] : 0u;
-    sum += c[i];
-  }
-  uint32_t total;
-  uint32_t ex = icount_prefix[t] + block_excl_scan<kEmT>(sum, total, s_w);
+    for (int i = 0; i < kEmI; ++i) {
+      c[i] = base + i < n ? tiles[srec[base + i]] : 0u;
+      sum += c[i];
+    }
+    uint32_t total;
+    uint32_t ex = icount_prefix[t] + block_excl_scan<kEmT>(sum, total, s_w);
 #pragma unroll
-  for (int i = 0; i < kEmI; ++i) {
-    if (base + i < n) ioff[base + i] = ex;
-    ex += c[i];
-  }
-  if (t == n_blocks - 1 && threadIdx.x == 0) {
-    const uint64_t n_inst = (uint64_t)icount_prefix[t] + total;
-    hdr->n_inst = n_inst;
-    if (n_inst > cap) set_status(hdr, kDevCapacity);
+    for (int i = 0; i < kEmI; ++i) {
+      if (base + i < n) ioff[base + i] = ex;
+      ex += c[i];
+    }
+    if (t == n_blocks - 1 && threadIdx.x == 0) {
+      const uint64_t n_inst = (uint64_t)icount_prefix[t] + total;
+      hdr->n_inst = n_inst;
+      if (n_inst > cap) set_status(hdr, kDevCapacity);
+    }
   }
 }
 
@@ -350,86 +360,89 @@ __global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restr
   const uint32_t nv = (uint32_t)hdr->n_visible;
   const uint64_t ni64 = hdr->n_inst;
   const uint32_t n_inst = (uint32_t)(ni64 < cap ? ni64 : cap);
-  const uint32_t s = blockIdx.x * kIsTile;
-  if (s >= n_inst || nv == 0) return;
-  for (int i = threadIdx.x; i < 256; i += kFlT) s_h[i] = 0;
-  for (int i = threadIdx.x; i < V; i += kFlT) {
-    s_recoff[i] = views[i].rec_off;
-    s_tileoff[i] = views[i].tile_off;
-    s_tilesx[i] = (uint32_t)views[i].tiles_x;
-  }
-  if (threadIdx.x < 32) {
-    // the last sorted record with ioff <= s, by a 32-way search: each round
-    // samples 32 offsets of [lo, hi) and keeps the span after the last one
-    // <= s (ioff[0] = 0 <= s, so lane 0's sample always qualifies)
-    const uint32_t lane = threadIdx.x;
-    uint32_t lo = 0, hi = nv;
-    while (hi - lo > 32) {
-      const uint32_t step = (hi - lo + 31) / 32;
-      const uint32_t idx = lo + lane * step;
+  if (nv == 0) return;
+  for (uint32_t b = blockIdx.x; (uint64_t)b * kIsTile < n_inst; b += gridDim.x) {
+    const uint32_t s = b * kIsTile;
+    __syncthreads();  // the shared arrays of the previous block are free
+    for (int i = threadIdx.x; i < 256; i += kFlT) s_h[i] = 0;
+    for (int i = threadIdx.x; i < V; i += kFlT) {
+      s_recoff[i] = views[i].rec_off;
+      s_tileoff[i] = views[i].tile_off;
+      s_tilesx[i] = (uint32_t)views[i].tiles_x;
+    }
+    if (threadIdx.x < 32) {
+      // the last sorted record with ioff <= s, by a 32-way search: each round
+      // samples 32 offsets of [lo, hi) and keeps the span after the last one
+      // <= s (ioff[0] = 0 <= s, so lane 0's sample always qualifies)
+      const uint32_t lane = threadIdx.x;
+      uint32_t lo = 0, hi = nv;
+      while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t idx = lo + lane * step;
+        const uint32_t m = __ballot_sync(kFull, idx < hi && ioff[idx] <= s);
+        lo += (31u - __clz(m)) * step;
+        hi = min(hi, lo + step);
+      }
+      const uint32_t idx = lo + lane;
       const uint32_t m = __ballot_sync(kFull, idx < hi && ioff[idx] <= s);
-      lo += (31u - __clz(m)) * step;
-      hi = min(hi, lo + step);
+      if (lane == 0) s_r0 = lo + 31u - __clz(m);
     }
-    const uint32_t idx = lo + lane;
-    const uint32_t m = __ballot_sync(kFull, idx < hi && ioff[idx] <= s);
-    if (lane == 0) s_r0 = lo + 31u - __clz(m);
-  }
-  __syncthreads();
-  const uint32_t r0 = s_r0;
-  for (uint32_t i = threadIdx.x; i <= (uint32_t)kIsTile; i += kFlT)
-    s_off[i] = r0 + i < nv ? ioff[r0 + i] : 0xffffffffu;
-  __syncthreads();
-  // kFlI consecutive instances per thread, walking the records
-  const uint32_t j0 = s + threadIdx.x * kFlI;
-  if (j0 < n_inst) {
-    int lo = 0, hi = kIsTile - 1;  // last i with s_off[i] <= j0 (s_off[0] <= s, s_off[K] > s + K - 1)
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= j0) lo = mid; else hi = mid - 1;
-    }
-    uint32_t i = (uint32_t)lo;
-    uint32_t rec = 0, x0 = 0, x1 = 0, tx = 0, ty = 0, vt = 0, vx = 0;
-    bool fresh = true;
-    for (int k = 0; k < kFlI; ++k) {
-      const uint32_t j = j0 + k;
-      if (j >= n_inst) break;
-      while (s_off[i + 1] <= j) {  // stays below K: s_off[K] > j
-        ++i;
-        fresh = true;
+    __syncthreads();
+    const uint32_t r0 = s_r0;
+    for (uint32_t i = threadIdx.x; i <= (uint32_t)kIsTile; i += kFlT)
+      s_off[i] = r0 + i < nv ? ioff[r0 + i] : 0xffffffffu;
+    __syncthreads();
+    // kFlI consecutive instances per thread, walking the records
+    const uint32_t j0 = s + threadIdx.x * kFlI;
+    if (j0 < n_inst) {
+      int lo = 0, hi = kIsTile - 1;  // last i with s_off[i] <= j0 (s_off[0] <= s, s_off[K] > s + K - 1)
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= j0) lo = mid; else hi = mid - 1;
       }
-      if (fresh) {
-        fresh = false;
-        rec = srec[r0 + i];
-        const uint2 rc = rect[rec];
-        x0 = rc.x & 0xFFFFu;
-        x1 = rc.y & 0xFFFFu;
-        const uint32_t w = x1 - x0, local = j - s_off[i];
-        tx = x0 + local % w;
-        ty = (rc.x >> 16) + local / w;
-        int vlo = 0, vhi = V - 1;  // view of the record: last view with rec_off <= rec
-        while (vlo < vhi) {
-          const int mid = (vlo + vhi + 1) >> 1;
-          if (s_recoff[mid] <= rec) vlo = mid; else vhi = mid - 1;
+      uint32_t i = (uint32_t)lo;
+      uint32_t rec = 0, x0 = 0, x1 = 0, tx = 0, ty = 0, vt = 0, vx = 0;
+      bool fresh = true;
+      for (int k = 0; k < kFlI; ++k) {
+        const uint32_t j = j0 + k;
+        if (j >= n_inst) break;
+        while (s_off[i + 1] <= j) {  // stays below K: s_off[K] > j
+          ++i;
+          fresh = true;
         }
-        vt = s_tileoff[vlo];
-        vx = s_tilesx[vlo];
-      }
-      const uint32_t gt = vt + ty * vx + tx;
-      ikey[j] = gt;
-      ival[j] = rec;
-      atomicAdd(&s_h[gt & 255u], 1u);
-      if (++tx == x1) {
-        tx = x0;
-        ++ty;
+        if (fresh) {
+          fresh = false;
+          rec = srec[r0 + i];
+          const uint2 rc = rect[rec];
+          x0 = rc.x & 0xFFFFu;
+          x1 = rc.y & 0xFFFFu;
+          const uint32_t w = x1 - x0, local = j - s_off[i];
+          tx = x0 + local % w;
+          ty = (rc.x >> 16) + local / w;
+          int vlo = 0, vhi = V - 1;  // view of the record: last view with rec_off <= rec
+          while (vlo < vhi) {
+            const int mid = (vlo + vhi + 1) >> 1;
+            if (s_recoff[mid] <= rec) vlo = mid; else vhi = mid - 1;
+          }
+          vt = s_tileoff[vlo];
+          vx = s_tilesx[vlo];
+        }
+        const uint32_t gt = vt + ty * vx + tx;
+        ikey[j] = gt;
+        ival[j] = rec;
+        atomicAdd(&s_h[gt & 255u], 1u);
+        if (++tx == x1) {
+          tx = x0;
+          ++ty;
+        }
       }
     }
+    __syncthreads();
+    // this block is block b of the first tile pass: its counts are
+    // written whole (no pass and no counts when the problem has one tile)
+    if (hist0)
+      for (int d = threadIdx.x; d < 256; d += kFlT) hist0[(size_t)b * 256 + d] = s_h[d];
   }
-  __syncthreads();
-  // this block is block blockIdx.x of the first tile pass: its counts are
-  // written whole (no pass and no counts when the problem has one tile)
-  if (hist0)
-    for (int d = threadIdx.x; d < 256; d += kFlT) hist0[(size_t)blockIdx.x * 256 + d] = s_h[d];
 }
 
 // ---------------------------------------------------------------- ranges
@@ -455,6 +468,10 @@ const uint32_t* sorted_instances(const Layout& L, const char* ws) {
   return (const uint32_t*)(ws + ((L.tile_passes & 1) ? L.ivB : L.ivA));
 }
 
+// grids of the radix passes (4 resident CTAs per SM) and of the emission
+// kernels; each loops over the blocks of work the device counts call for
+constexpr uint32_t kPassGrid = 152 * 4, kEmitGrid = 152 * 8;
+
 cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaStream_t st) {
   (void)cfg;
   Header* hdr = (Header*)(ws + L.header);
@@ -473,7 +490,8 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* cvA = (uint32_t*)(ws + L.cvA);
   uint32_t* ckB = (uint32_t*)(ws + L.ckB);
   uint32_t* cvB = (uint32_t*)(ws + L.cvB);
-  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, vis, vis_prefix, L.n_cmp_tiles, 1, nullptr);
+  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, vis, vis_prefix, L.n_cmp_tiles, 1, nullptr,
+                   nullptr, 0u, 1u);
   const size_t hd_stride = (size_t)L.n_dsort_tiles * 256;
   launch_dependent(compact_kernel, dim3(L.n_cmp_tiles), dim3(kCmpT), 0, st, tiles, (const uint32_t*)(ws + L.key), L.R, vis_prefix, ckA, cvA,
                                                   hd, hdr);
@@ -483,8 +501,9 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
     const bool even = (p & 1) == 0;
     uint32_t* hp = hd + p * hd_stride;
     const bool last = p == 3;
-    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_dsort_tiles, 256, ghist + 256 * p);
-    launch_dependent(downsweep_kernel<kDsTile>, dim3(L.n_dsort_tiles), dim3(kOsT), 0, st, even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
+    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_dsort_tiles, 256, ghist + 256 * p,
+                     (const uint64_t*)&hdr->n_visible, L.R, (uint32_t)kDsTile);
+    launch_dependent(downsweep_kernel<kDsTile>, dim3(min(L.n_dsort_tiles, kPassGrid)), dim3(kOsT), 0, st, even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
                                                        even ? cvB : cvA, &hdr->n_visible, L.R, 8 * p, ghist + 256 * p,
                                                        hp, last ? nullptr : hp + hd_stride, last ? icount : nullptr,
                                                        tiles);
@@ -494,10 +513,11 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* ikB = (uint32_t*)(ws + L.ikB);
   uint32_t* ivB = (uint32_t*)(ws + L.ivB);
   const ViewDev* views = (const ViewDev*)(ws + L.views);
-  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, icount, icount, L.n_emit_tiles, 1, nullptr);
+  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, icount, icount, L.n_emit_tiles, 1, nullptr,
+                   (const uint64_t*)&hdr->n_visible, L.R, (uint32_t)kEmTile);
   uint32_t* ioff = (uint32_t*)(ws + L.ioff);
-  launch_dependent(emit_offsets_kernel, dim3(L.n_emit_tiles), dim3(kEmT), 0, st, cvA, tiles, icount, ioff, L.cap, hdr);
-  launch_dependent(emit_fill_kernel, dim3(L.n_isort_tiles), dim3(kFlT), 0, st, cvA, ioff, (const uint2*)(ws + L.rect), views, L.V, L.cap,
+  launch_dependent(emit_offsets_kernel, dim3(min(L.n_emit_tiles, kEmitGrid)), dim3(kEmT), 0, st, cvA, tiles, icount, ioff, L.cap, hdr);
+  launch_dependent(emit_fill_kernel, dim3(min(L.n_isort_tiles, kEmitGrid)), dim3(kFlT), 0, st, cvA, ioff, (const uint2*)(ws + L.rect), views, L.V, L.cap,
                                                      ikA, ivA, L.tile_passes > 0 ? hi : nullptr, hdr);
   uint32_t* gh_tile = ghist + 4 * 256;
   const size_t hi_stride = (size_t)L.n_isort_tiles * 256;
@@ -505,8 +525,9 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
     const bool even = (p & 1) == 0;
     uint32_t* hp = hi + p * hi_stride;
     const bool last = p == L.tile_passes - 1;
-    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_isort_tiles, 256, gh_tile + 256 * p);
-    launch_dependent(downsweep_kernel<kIsTile>, dim3(L.n_isort_tiles), dim3(kOsT), 0, st, even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
+    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_isort_tiles, 256, gh_tile + 256 * p,
+                     (const uint64_t*)&hdr->n_inst, L.cap, (uint32_t)kIsTile);
+    launch_dependent(downsweep_kernel<kIsTile>, dim3(min(L.n_isort_tiles, kPassGrid)), dim3(kOsT), 0, st, even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
                                                        even ? ivB : ivA, &hdr->n_inst, L.cap, 8 * p,
                                                        gh_tile + 256 * p, hp, last ? nullptr : hp + hi_stride,
                                                        nullptr, nullptr);

@@ -132,7 +132,8 @@ class Rasterizer:
         need = U.ubs_workspace_size(self.problem)
         if need == 0:
             raise ValueError("invalid problem (ubs_workspace_size returned 0)")
-        if self._ws is None or self.ws_bytes < need:
+        if self._ws is None or self.ws_bytes < need or 2 * need < self.ws_bytes:  # grown, or far too big
+            self._ws = None
             self._ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
             base = self._ws.data_ptr()
             self.ws_ptr = (base + 255) // 256 * 256
@@ -180,14 +181,19 @@ class Rasterizer:
 
     def forward(self, check: bool = True, image=None):
         """Full forward.  With ``check`` the call synchronises once to read the
-        device status and, if the instance capacity was too small, grows it
-        and runs preprocess/bin_sort again."""
+        device status and fits the instance capacity to the count found: it
+        grows it when it was too small, and shrinks it when it is more than
+        four times the count (the capacity sizes the instance buffers and the
+        per-pass counts), then runs preprocess/bin_sort again.  Later calls
+        without ``check`` (and captured graphs) keep the capacity."""
         self.preprocess()
         self.bin_sort()
         if check:
             st = self.status()
-            if st.status == U.UBS_ERR_CAPACITY:
-                self.set_capacity(int(st.instances * 1.25) + 1024)
+            need = int(st.instances)
+            refit = st.status == U.UBS_ERR_CAPACITY or (st.status == U.UBS_OK and self.capacity > 4 * need + (1 << 16))
+            if refit:
+                self.set_capacity(int(need * 1.25) + (1 << 16))
                 self.preprocess()
                 self.bin_sort()
                 st = self.status()
