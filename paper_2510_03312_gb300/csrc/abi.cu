@@ -113,6 +113,12 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.vis_count = take((size_t)L.n_cmp_tiles * 4);
   L.vis_prefix = take((size_t)L.n_cmp_tiles * 4);
   L.ioff = take((size_t)L.R * 4);
+  // the primitives some view sees, per scene (kept outside the region that
+  // ubs_bin_sort zeroes below)
+  uint64_t Ptot = 0;
+  for (int sc = 0; sc < pr->n_scenes; ++sc) Ptot += (uint64_t)pr->scenes[sc].P;
+  L.act_list = take((size_t)Ptot * 4);
+  L.act_count = take((size_t)kMaxScenes * 4);
   // per-pass counts, rewritten whole by every ubs_bin_sort
   L.hist_d = take((size_t)4 * L.n_dsort_tiles * 256 * 4);
   L.hist_i = take((size_t)L.tile_passes * L.n_isort_tiles * 256 * 4);
@@ -217,6 +223,8 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
   char* w = (char*)ws;
   cudaError_t e = cudaMemsetAsync(w + L.header, 0, sizeof(Header), stream);
   if (e != cudaSuccess) return UBS_ERR_CUDA;
+  e = cudaMemsetAsync(w + L.act_count, 0, (size_t)L.S * 4, stream);
+  if (e != cudaSuccess) return UBS_ERR_CUDA;
   e = cudaMemsetAsync(w + L.vis_count, 0, (size_t)L.n_cmp_tiles * 4, stream);
   if (e != cudaSuccess) return UBS_ERR_CUDA;
   // view table: per-view constants, tile/record/pixel offsets
@@ -253,10 +261,13 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
     if (e != cudaSuccess) return UBS_ERR_CUDA;
   }
   const CfgDev cfg = cfg_dev(pr->cfg);
+  uint64_t act_off = 0;
   for (int s = 0; s < L.S; ++s) {
     ViewList vl;
     view_list(pr, s, vl);
-    e = launch_preprocess(scene_dev(pr->scenes[s]), vl, views, cfg, L, w, stream);
+    e = launch_preprocess(scene_dev(pr->scenes[s]), vl, views, cfg, L, w, (uint32_t*)(w + L.act_list) + act_off,
+                          (uint32_t*)(w + L.act_count) + s, stream);
+    act_off += (uint64_t)pr->scenes[s].P;
     if (e != cudaSuccess) return UBS_ERR_CUDA;
   }
   return UBS_OK;
@@ -299,13 +310,17 @@ ubs_status ubs_render_bwd_params(const ubs_problem* pr, void* ws, size_t ws_byte
   char* w = (char*)ws;
   const CfgDev cfg = cfg_dev(pr->cfg);
   const ViewDev* views = (const ViewDev*)(w + L.views);
+  uint64_t act_off = 0;
   for (int s = 0; s < L.S; ++s) {
     ViewList vl;
     view_list(pr, s, vl);
     const ubs_scene_grad& g = grads[s];
     SceneGradDev gd = {g.mean_x, g.mean_q, g.rot, g.scale_x, g.L_qx, g.L_q, g.b, g.opacity, g.rgb};
-    if (launch_prim_backward(scene_dev(pr->scenes[s]), gd, vl, views, cfg, L, w, stream) != cudaSuccess)
+    if (launch_prim_backward(scene_dev(pr->scenes[s]), gd, vl, views, cfg, L, w,
+                             (const uint32_t*)(w + L.act_list) + act_off, (const uint32_t*)(w + L.act_count) + s,
+                             stream) != cudaSuccess)
       return UBS_ERR_CUDA;
+    act_off += (uint64_t)pr->scenes[s].P;
   }
   return UBS_OK;
 }

@@ -96,6 +96,8 @@ struct Layout {
   size_t hist_i;     // the same for the tile-key passes [tile_passes][n_isort_tiles][256]
   size_t icount;     // instances per emission block [n_emit_tiles]
   size_t ghist;      // digit totals per pass [4 + 3][256]
+  size_t act_list;   // per scene (at the sum of the earlier scenes' P): primitives visible in some view
+  size_t act_count;  // their number per scene [kMaxScenes]
   size_t Tfin, last, pairs;
   size_t total;
 };

@@ -37,8 +37,10 @@ struct ViewList {
   int16_t idx[kMaxViews];
 };
 
+// act_list/act_count: the scene's list of primitives visible in some view
+// (appended by preprocess, read by the parameter backward)
 cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const ViewDev* views, const CfgDev& cfg,
-                              const Layout& L, char* ws, cudaStream_t st);
+                              const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, cudaStream_t st);
 
 // scan/sort/emit/ranges; leaves the sorted instance records in the buffer
 // reported by sorted_instances()
@@ -48,6 +50,7 @@ const uint32_t* sorted_instances(const Layout& L, const char* ws);
 cudaError_t launch_render_fwd(const Layout& L, const CfgDev& cfg, char* ws, float* image, cudaStream_t st);
 cudaError_t launch_render_bwd(const Layout& L, const CfgDev& cfg, char* ws, const float* dL_dimage, cudaStream_t st);
 cudaError_t launch_prim_backward(const SceneDev& sc, const SceneGradDev& g, const ViewList& vl, const ViewDev* views,
-                                 const CfgDev& cfg, const Layout& L, char* ws, cudaStream_t st);
+                                 const CfgDev& cfg, const Layout& L, char* ws, const uint32_t* act_list,
+                                 const uint32_t* act_count, cudaStream_t st);
 
 }  // namespace ubs

@@ -34,7 +34,8 @@ template <int C>
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList vl, const ViewDev* __restrict__ views,
                                                          CfgDev cfg, float4* __restrict__ rec4,
                                                          uint32_t* __restrict__ key, uint32_t* __restrict__ tiles,
-                                                         uint2* __restrict__ rect, uint32_t* __restrict__ vis_count) {
+                                                         uint2* __restrict__ rect, uint32_t* __restrict__ vis_count,
+                                                         uint32_t* __restrict__ act_list, uint32_t* act_count) {
   wait_prior_grid();
   extern __shared__ ViewDev s_views[];
   for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
@@ -46,10 +47,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList v
   PrimVI<C> vi;
   prim_stage<C>(in, sc.rot_mode, vi);
   const float cr = __ldg(sc.rgb + p), cg = __ldg(sc.rgb + sc.P + p), cb = __ldg(sc.rgb + 2 * sc.P + p);
+  bool any = false;  // visible in some view
   for (int k = 0; k < vl.n; ++k) {
     const ViewDev& v = s_views[k];
     ViewOut o;
     view_stage<C>(in, vi, v, cfg, o);
+    any = any || o.valid;
     const uint32_t r = v.rec_off + (uint32_t)p;
     tiles[r] = o.tiles;
     {
@@ -68,10 +71,23 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList v
       rec4[3 * (size_t)r + 2] = make_float4(vi.beta_x, cr, cg, cb);
     }
   }
+  // scenes with several views: the primitives some view sees, listed for the
+  // parameter backward (one add per warp)
+  if (vl.n > 1) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, any);
+    if (m) {
+      const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(act_count, (uint32_t)__popc(m));
+      base = __shfl_sync(act, base, leader);
+      if (any) act_list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)p;
+    }
+  }
 }
 
 cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const ViewDev* views, const CfgDev& cfg,
-                              const Layout& L, char* ws, cudaStream_t st) {
+                              const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, cudaStream_t st) {
   if (sc.P == 0 || vl.n == 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = (unsigned)((sc.P + threads - 1) / threads);
@@ -82,10 +98,10 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
   uint2* rect = (uint2*)(ws + L.rect);
   uint32_t* vis = (uint32_t*)(ws + L.vis_count);
   switch (sc.N) {
-    case 3: launch_dependent(preprocess_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
-    case 4: launch_dependent(preprocess_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
-    case 6: launch_dependent(preprocess_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
-    case 7: launch_dependent(preprocess_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis); break;
+    case 3: launch_dependent(preprocess_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
+    case 4: launch_dependent(preprocess_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
+    case 6: launch_dependent(preprocess_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
+    case 7: launch_dependent(preprocess_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
