@@ -9,6 +9,8 @@
 // Sigma_qx, beta) and then loops over the scene's views, so each primitive's
 // parameters are read from HBM once per batch of views.  Parameter planes
 // are structure-of-arrays: a warp reads 32 consecutive floats per plane.
+#include <atomic>
+
 #include "kernels.cuh"
 #include "prim_forward.cuh"
 
@@ -86,9 +88,157 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList v
   }
 }
 
+// Scenes with query dimensions (N > 3): the conditioning runs per (view,
+// primitive) as in preprocess_kernel, but only the records that pass the
+// early tests (view_candidate) are projected, from a per-warp queue in
+// shared memory, 32 at a time.  Where the query culls most records (o(q)
+// below alpha_min), the projection -- over half of a record's arithmetic --
+// then runs on full warps instead of on the few lanes whose record survives.
+// The projection of a queued record is the same arithmetic on the same
+// values as in view_stage.
+constexpr int kQCap = 64;   // queue entries per warp: 31 carried over + 32 new
+constexpr int kQWarps = 8;  // warps per CTA (256 threads)
+
+template <int C>
+__global__ void __launch_bounds__(256) preprocess_queued_kernel(SceneDev sc, ViewList vl,
+                                                                const ViewDev* __restrict__ views, CfgDev cfg,
+                                                                float4* __restrict__ rec4, uint32_t* __restrict__ key,
+                                                                uint32_t* __restrict__ tiles, uint2* __restrict__ rect,
+                                                                uint32_t* __restrict__ vis_count,
+                                                                uint32_t* __restrict__ act_list, uint32_t* act_count) {
+  wait_prior_grid();
+  extern __shared__ ViewDev s_views[];
+  // per warp: the lanes' view-independent values (mean, Sigma, beta_x, rgb),
+  // and the queue (record, view | owner lane << 16, shift, o(q))
+  __shared__ float s_prim[kQWarps][13][32];
+  __shared__ float s_qf[kQWarps][4][kQCap];
+  __shared__ uint32_t s_qr[kQWarps][kQCap], s_qk[kQWarps][kQCap];
+  __shared__ uint32_t s_any[kQWarps];
+  for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
+  if (threadIdx.x < kQWarps) s_any[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < sc.P;  // every lane stays: the queue is warp-synchronous
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  float(*prim)[32] = s_prim[w];
+  float(*qf)[kQCap] = s_qf[w];
+  uint32_t* qr = s_qr[w];
+  uint32_t* qk = s_qk[w];
+  PrimIn<C> in;
+  PrimVI<C> vi;
+  if (live) {
+    load_prim<C>(sc, p, in);
+    prim_stage<C>(in, sc.rot_mode, vi);
+    for (int i = 0; i < 3; ++i) prim[i][lane] = in.mx[i];
+    for (int i = 0; i < 6; ++i) prim[3 + i][lane] = vi.Sc[i];
+    prim[9][lane] = vi.beta_x;
+    for (int i = 0; i < 3; ++i) prim[10 + i][lane] = __ldg(sc.rgb + i * sc.P + p);
+  }
+  __syncwarp();
+  // projects queue entry j (any lane may take any entry)
+  auto project = [&](int j) {
+    const uint32_t r = qr[j], kk = qk[j];
+    const int k = (int)(kk & 0xffffu), owner = (int)(kk >> 16);
+    float mx[3], Sc[6];
+    ViewCond c;
+    for (int i = 0; i < 3; ++i) {
+      mx[i] = prim[i][owner];
+      c.shift[i] = qf[i][j];
+      c.mc[i] = mx[i] + c.shift[i];
+    }
+    c.oq = qf[3][j];
+    for (int i = 0; i < 6; ++i) Sc[i] = prim[3 + i][owner];
+    const float beta_x = prim[9][owner];
+    ViewOut o;
+    view_project(mx, Sc, beta_x, true, c, s_views[k], cfg, o);
+    tiles[r] = o.tiles;
+    {
+      // visible records per compaction block (one add per group of lanes)
+      const unsigned act = __activemask();
+      const uint32_t blk = r / kCmpTile;
+      const unsigned peers = __match_any_sync(act, blk);
+      const unsigned vis = __ballot_sync(act, o.valid) & peers;
+      if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1) && vis) atomicAdd(vis_count + blk, (uint32_t)__popc(vis));
+    }
+    if (o.valid) {
+      key[r] = __float_as_uint(o.depth);
+      rect[r] = make_uint2((uint32_t)o.tx0 | ((uint32_t)o.ty0 << 16), (uint32_t)o.tx1 | ((uint32_t)o.ty1 << 16));
+      rec4[3 * (size_t)r + 0] = make_float4(o.mu_hi[0], o.mu_hi[1], o.mu_lo[0], o.mu_lo[1]);
+      rec4[3 * (size_t)r + 1] = make_float4(o.conic[0], o.conic[1], o.conic[2], log2f(o.oq));
+      rec4[3 * (size_t)r + 2] = make_float4(beta_x, prim[10][owner], prim[11][owner], prim[12][owner]);
+      atomicOr(&s_any[w], 1u << owner);
+    }
+  };
+  int qn = 0;  // warp-uniform
+  for (int k = 0; k < vl.n; ++k) {
+    const ViewDev& v = s_views[k];
+    bool cand = false;
+    ViewCond c;
+    uint32_t r = 0;
+    if (live) {
+      view_condition<C>(in, vi, v, c);
+      r = v.rec_off + (uint32_t)p;
+      cand = view_candidate(vi.valid, c, v, cfg);
+      if (!cand) tiles[r] = 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, cand);
+    if (cand) {
+      const int j = qn + __popc(m & lt);
+      qr[j] = r;
+      qk[j] = (uint32_t)k | ((uint32_t)lane << 16);
+      for (int i = 0; i < 3; ++i) qf[i][j] = c.shift[i];
+      qf[3][j] = c.oq;
+    }
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {  // the 32 newest entries, one per lane
+      project(qn - 32 + lane);
+      qn -= 32;
+      __syncwarp();
+    }
+  }
+  if (lane < qn) project(lane);
+  __syncwarp();
+  // scenes with several views: the primitives some view sees, listed for the
+  // parameter backward (one add per warp)
+  const bool any = live && ((s_any[w] >> lane) & 1u);
+  if (vl.n > 1) {
+    const unsigned m = __ballot_sync(0xffffffffu, any);
+    if (m) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(act_count, (uint32_t)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (any) act_list[base + __popc(m & lt)] = (uint32_t)p;
+    }
+  }
+}
+
+constexpr int kMaxDevices = 64;
+std::atomic<bool> g_queued_smem_set[kMaxDevices];
+
+// the queued kernels' view table plus their static queues can pass 48 KB of
+// shared memory (256 views): opt in once per device
+cudaError_t prepare_queued() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices && g_queued_smem_set[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  const int bytes = (int)(kMaxViews * sizeof(ViewDev));
+  e = cudaFuncSetAttribute(preprocess_queued_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(preprocess_queued_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(preprocess_queued_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) g_queued_smem_set[dev].store(true, std::memory_order_release);
+  return e;
+}
+
 cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const ViewDev* views, const CfgDev& cfg,
                               const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, cudaStream_t st) {
   if (sc.P == 0 || vl.n == 0) return cudaSuccess;
+  if (sc.N > 3) {
+    const cudaError_t e = prepare_queued();
+    if (e != cudaSuccess) return e;
+  }
   const int threads = 256;
   const unsigned blocks = (unsigned)((sc.P + threads - 1) / threads);
   const size_t smem = sizeof(ViewDev) * vl.n;
@@ -99,9 +249,9 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
   uint32_t* vis = (uint32_t*)(ws + L.vis_count);
   switch (sc.N) {
     case 3: launch_dependent(preprocess_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
-    case 4: launch_dependent(preprocess_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
-    case 6: launch_dependent(preprocess_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
-    case 7: launch_dependent(preprocess_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
+    case 4: launch_dependent(preprocess_queued_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
+    case 6: launch_dependent(preprocess_queued_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
+    case 7: launch_dependent(preprocess_queued_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -217,9 +217,16 @@ struct ViewOut {
   float oq;
 };
 
+// The conditioning of one record on its view's query (Sec. 4.3, 4.4): the
+// modulated opacity o(q), the mean shift and the conditioned mean.
+struct ViewCond {
+  float oq;
+  float shift[3];
+  float mc[3];
+};
+
 template <int C>
-UBS_HD void view_stage(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& v, const CfgDev& cfg,
-                       ViewOut& out) {
+UBS_HD void view_condition(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& v, ViewCond& cond) {
   const float* Rv = v.R;
   float mc[3], shift[3] = {0.0f, 0.0f, 0.0f};
   float oq = in.o;
@@ -260,10 +267,37 @@ UBS_HD void view_stage(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& 
   } else {
     for (int i = 0; i < 3; ++i) mc[i] = in.mx[i];
   }
+  cond.oq = oq;
+  for (int i = 0; i < 3; ++i) {
+    cond.shift[i] = shift[i];
+    cond.mc[i] = mc[i];
+  }
+}
+
+// Whether a conditioned record can be drawn at all: the tests of
+// view_project that come before its projection (kernel valid, o(q) at least
+// alpha_min, depth beyond the near plane), with the same arithmetic.
+UBS_HD bool view_candidate(bool kernel_valid, const ViewCond& c, const ViewDev& v, const CfgDev& cfg) {
+  const float* Rv = v.R;
+  const float tz = ((Rv[6] * c.mc[0] + Rv[7] * c.mc[1]) + Rv[8] * c.mc[2]) + v.t[2];
+  return kernel_valid && (tz > cfg.near_plane) && (c.oq >= cfg.amin);
+}
+
+// The projection of a conditioned record (Sec. 3, EWA splatting of the Beta
+// kernel): depth, screen mean, conic, tight support radius and tile
+// rectangle, and the error-free screen mean.  mx: the primitive's spatial
+// mean; Sc, beta_x, kernel_valid: its view-independent covariance, spatial
+// exponent and validity.
+UBS_HD void view_project(const float* mx, const float* Sc, float beta_x, bool kernel_valid, const ViewCond& c,
+                         const ViewDev& v, const CfgDev& cfg, ViewOut& out) {
+  const float* Rv = v.R;
+  const float* mc = c.mc;
+  const float* shift = c.shift;
+  const float oq = c.oq;
   float tc[3];
   for (int j = 0; j < 3; ++j) tc[j] = ((Rv[3 * j] * mc[0] + Rv[3 * j + 1] * mc[1]) + Rv[3 * j + 2] * mc[2]) + v.t[j];
   const float tz = tc[2];
-  bool valid = vi.valid && (tz > cfg.near_plane);
+  bool valid = kernel_valid && (tz > cfg.near_plane);
   const float tzs = valid ? tz : 1.0f;
   const float u = tc[0] / tzs;
   const float vq = tc[1] / tzs;
@@ -282,7 +316,7 @@ UBS_HD void view_stage(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& 
     T[0][j] = J00 * Rv[j] + J02 * Rv[6 + j];
     T[1][j] = J11 * Rv[3 + j] + J12 * Rv[6 + j];
   }
-  const float* S = vi.Sc;
+  const float* S = Sc;
   float U[2][3];
   for (int a = 0; a < 2; ++a)
     for (int j = 0; j < 3; ++j)
@@ -301,7 +335,7 @@ UBS_HD void view_stage(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& 
   if (cfg.flags & 1) {
     const float oqs = valid ? oq : 1.0f;
     const float lr = spec::log32(cfg.amin / oqs);
-    rcut = 1.0f - spec::exp32(lr / vi.beta_x);
+    rcut = 1.0f - spec::exp32(lr / beta_x);
   }
   const float ex = sqrtf(fmaxf(rcut * s00, 0.0f));
   const float ey = sqrtf(fmaxf(rcut * s11, 0.0f));
@@ -332,7 +366,7 @@ UBS_HD void view_stage(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& 
   }
   // error-free screen mean: m = mx + shift exactly, t = Rv m + t, mu' = f t/t_z + c
   DF m[3];
-  for (int i = 0; i < 3; ++i) m[i] = two_sum(in.mx[i], shift[i]);
+  for (int i = 0; i < 3; ++i) m[i] = two_sum(mx[i], shift[i]);
   DF t3[3];
   for (int j = 0; j < 3; ++j) {
     DF acc = {v.t[j], 0.0f};
@@ -352,6 +386,14 @@ UBS_HD void view_stage(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& 
   out.mu_lo[0] = mx2.lo;
   out.mu_hi[1] = my2.hi;
   out.mu_lo[1] = my2.lo;
+}
+
+template <int C>
+UBS_HD void view_stage(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& v, const CfgDev& cfg,
+                       ViewOut& out) {
+  ViewCond c;
+  view_condition<C>(in, vi, v, c);
+  view_project(in.mx, vi.Sc, vi.beta_x, vi.valid, c, v, cfg, out);
 }
 
 }  // namespace ubs
