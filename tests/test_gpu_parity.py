@@ -198,6 +198,23 @@ def test_very_long_tile_lists():
     check_grads(gpu, orc, ref, tiles=tiles)
 
 
+@pytest.mark.parametrize("n_views,N", [(40, 6), (256, 7), (40, 3)])
+def test_many_views_of_one_scene(n_views, N):
+    """More views than one 32-view mask of the parameter backward, up to the
+    256-view limit (the largest view table in shared memory)."""
+    rng = np.random.default_rng(70 + n_views + N)
+    sc = S.make_scene(71, N, 1500, means="clusters", extent=2.0, n_clusters=4, rng=rng)
+    views = S.sphere_views(rng, n_views, 5.0, 24, 20, hemisphere=True, times=list(rng.uniform(0, 1, n_views)))
+    cfg = S.RasterConfig()
+    orc = R64.Oracle([sc], views, cfg)
+    gpu = gpu_forward([sc], views, cfg)
+    assert gpu["status"].visible_records > 0
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    _, _, ref = check_images(gpu, orc, recs=recs)
+    check_grads(gpu, orc, ref)
+
+
 def test_full_size_static_sampled():
     """The 1M-primitive 1600x1060 workload in the launch configuration the
     benchmark times: all records and instance lists bit-exact, images and
