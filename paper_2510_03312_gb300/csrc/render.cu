@@ -96,8 +96,10 @@ __device__ __forceinline__ void eval_pair(float lx, float ly, const float4& p, c
   e.dy = __fsub_rn(ly, p.y);
   const float t = __fmaf_rn(p.z, e.dx, __fmul_rn(p.w, e.dy));
   e.r = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(q.x, e.dy), e.dy));
-  e.om = __fsub_rn(1.0f, e.r);
-  e.lg = lg2_approx(fmaxf(e.om, 0.0f));
+  // 1 - r, held above 0: a pair with r < 1 has 1 - r >= 2^-24 and is
+  // unchanged; for the others (never composited) log2 and 1/(1 - r) stay finite
+  e.om = fmaxf(__fsub_rn(1.0f, e.r), 1.0e-30f);
+  e.lg = lg2_approx(e.om);
   e.alpha = fminf(amax, ex2_approx(__fmaf_rn(q.z, e.lg, q.y)));
   e.use = (e.r < 1.0f) && (e.alpha >= amin);
 }
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(32)
         B1[k] = fmaf(a, d1, B1[k]);
         B2[k] = fmaf(a, d2, B2[k]);
         const float ga = a < cfg.amax ? dalpha * a : 0.0f;
-        const float qq = use[k] ? __fdividef(ga, e[k].om) : 0.0f;  // 1 - r > 0 for a composited pair
+        const float qq = __fdividef(ga, e[k].om);  // ga = 0 unless composited; 1 - r > 0
         const float u0 = qq * e[k].dx, u1 = qq * e[k].dy;
         gv[0] += u0;
         gv[1] += u1;
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(32)
         gv[3] = fmaf(u0, e[k].dy, gv[3]);
         gv[4] = fmaf(u1, e[k].dy, gv[4]);
         gv[5] += ga;
-        gv[6] = fmaf(ga, use[k] ? e[k].lg : 0.0f, gv[6]);
+        gv[6] = fmaf(ga, e[k].lg, gv[6]);
       }
       if (__popc(hits) == 1) {  // one lane: its values are the totals
         if (any) {
