@@ -110,6 +110,7 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.ikB = take((size_t)L.cap * 4);
   L.ivB = take((size_t)L.cap * 4);
   L.tstart = take((size_t)(L.NT + 1) * 4);
+  L.tile_order = take((size_t)L.NT * 4);
   L.vis_count = take((size_t)L.n_cmp_tiles * 4);
   L.vis_prefix = take((size_t)L.n_cmp_tiles * 4);
   L.ioff = take((size_t)L.R * 4);
@@ -124,6 +125,7 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.hist_i = take((size_t)L.tile_passes * L.n_isort_tiles * 256 * 4);
   L.icount = take((size_t)L.n_emit_tiles * 4);
   L.ghist = take(7 * 256 * 4);
+  L.order_count = take(2 * 132 * 4);  // zeroed with the per-pass counts
   L.Tfin = take((size_t)L.NPIX * 4);
   L.last = take((size_t)L.NPIX * 4);
   L.pairs = take((size_t)L.NPIX * 4);

@@ -88,6 +88,8 @@ struct Layout {
   size_t ckA, cvA, ckB, cvB;
   size_t ikA, ivA, ikB, ivB;
   size_t tstart;
+  size_t tile_order;   // the order the blend kernels take the tiles in [NT]
+  size_t order_count;  // tiles per list-length bucket and bucket cursors [2 x 132]
   size_t vis_count;  // visible records per compaction block [n_cmp_tiles] (made by preprocess)
   size_t vis_prefix; // its exclusive prefix [n_cmp_tiles]
   size_t ioff;       // first instance of each depth-sorted record [R]

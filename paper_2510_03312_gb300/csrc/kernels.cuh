@@ -15,6 +15,19 @@ namespace ubs {
 // launched without the attribute).  Every kernel waiting first keeps the
 // ordering transitive.
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Whether the blend kernels take the tiles in the order of bin_sort's tile
+// order (longest lists first) or in their own order: reordering pays where
+// lists are long on average (a few long tiles would otherwise trail the
+// grid) and costs locality where they are short.
+constexpr uint32_t kOrdDense = 64;  // instances per tile from which the tiles are reordered
+__device__ __forceinline__ bool order_dense(const Header* hdr, uint32_t NT, uint32_t cap) {
+  const uint64_t n = hdr->n_inst < cap ? hdr->n_inst : cap;
+  return n >= (uint64_t)kOrdDense * NT;
+}
+// whether the lists can be dense at all with the layout's instance capacity:
+// where not, no order is made and the blend kernels get none
+inline bool order_possible(const Layout& L) { return (uint64_t)L.cap >= (uint64_t)kOrdDense * L.NT; }
+
 template <typename... Params, typename... Args>
 cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              Args... args) {

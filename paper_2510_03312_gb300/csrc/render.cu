@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
     render_fwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       float* __restrict__ image, float* __restrict__ Tfin, uint32_t* __restrict__ lastc,
-                      const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs) {
+                      const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs,
+                      const uint32_t* __restrict__ tile_order, uint32_t n_tiles, uint32_t cap) {
   wait_prior_grid();
   constexpr int B = TW * TH;
   constexpr int BS = B < 256 ? B : 256;  // records staged per batch
@@ -185,7 +186,9 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
   __shared__ uint8_t s_list[NW][BS];
   __shared__ int s_v;
   if (hdr->status != 0) return;
-  const uint32_t g = blockIdx.x;
+  // the tile order where there is one (long lists on average): the header
+  // is at hand already, the order costs one more dependent load
+  const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x] : blockIdx.x;
   if (threadIdx.x == 0) s_v = find_view(views, V, g);
   __syncthreads();
   const ViewDev& v = views[s_v];
@@ -348,7 +351,8 @@ __global__ void __launch_bounds__(32)
     render_bwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       const float* __restrict__ dLdimg, const float* __restrict__ Tfin,
-                      const uint32_t* __restrict__ lastc, float4* __restrict__ g2d, const Header* hdr, uint32_t R) {
+                      const uint32_t* __restrict__ lastc, float4* __restrict__ g2d, const Header* hdr, uint32_t R,
+                      const uint32_t* __restrict__ tile_order, uint32_t n_tiles, uint32_t cap) {
   wait_prior_grid();
   constexpr int WB = 32;             // entries per batch: one per lane
   constexpr int BPT = TW * TH / 64;  // 8x8 blocks per tile
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(32)
   __shared__ float s_acc[10][WB + 1];  // +1: the 10 writer lanes hit 10 different banks
   __shared__ uint8_t s_list[WB];
   if (hdr->status != 0) return;
-  const uint32_t g = blockIdx.x / BPT;
+  const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x / BPT] : blockIdx.x / BPT;
   const int wb = blockIdx.x % BPT;
   const int lane = threadIdx.x;
   const ViewDev& v = views[find_view(views, V, g)];
@@ -517,10 +521,12 @@ cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cu
   constexpr int NT = TW * TH;
   if (cfg.flags & 2)  // diagnostic variant: also count visited pairs with r < 1 per pixel
     launch_dependent(render_fwd_kernel<TW, TH, true>, dim3(L.NT), dim3(NT), 0, st, views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
-                                                       image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs));
+                                                       image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs),
+                                                       order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr, L.NT, L.cap);
   else
     launch_dependent(render_fwd_kernel<TW, TH, false>, dim3(L.NT), dim3(NT), 0, st, views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
-                                                        image, Tfin, last, hdr, R, nullptr);
+                                                        image, Tfin, last, hdr, R, nullptr,
+                                                        order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr, L.NT, L.cap);
   return cudaGetLastError();
 }
 
@@ -529,7 +535,8 @@ cudaError_t bwd_t(const Layout& L, const CfgDev& cfg, char* ws, const float* dL,
   launch_dependent(render_bwd_kernel<TW, TH>, dim3(L.NT * (TW * TH / 64)), dim3(32), 0, st, 
       (const ViewDev*)(ws + L.views), L.V, cfg, (const uint32_t*)(ws + L.tstart), sorted_instances(L, ws),
       (const float4*)(ws + L.rec4), dL, (const float*)(ws + L.Tfin), (const uint32_t*)(ws + L.last),
-      (float4*)(ws + L.g2d), (const Header*)(ws + L.header), L.R > 0 ? L.R : 1);
+      (float4*)(ws + L.g2d), (const Header*)(ws + L.header), L.R > 0 ? L.R : 1,
+      order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr, L.NT, L.cap);
   return cudaGetLastError();
 }
 

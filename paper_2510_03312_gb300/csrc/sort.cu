@@ -462,6 +462,131 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ skeys, const uint64_t
   }
 }
 
+// ---------------------------------------------------------------- tile order
+
+constexpr int kOrdT = 1024, kOrdBuckets = 4 * 33;
+
+// bucket of a list length: four per octave, longest first (bucket 0)
+__device__ __forceinline__ int length_bucket(uint32_t n) {
+  if (n == 0) return kOrdBuckets - 1;
+  const int e = 31 - __clz(n);                                                       // 2^e <= n
+  const int f = e >= 2 ? (int)((n >> (e - 2)) & 3u) : (int)((n << (2 - e)) & 3u);  // the next two bits
+  return kOrdBuckets - 2 - (4 * e + f);
+}
+
+// Warp-aggregated add of 1 to s[b] (b < 0: no add): the lanes sharing a
+// bucket make one shared-memory atomic, and each gets its rank among the
+// lanes that came before it in the warp; returns the old value plus the rank.
+__device__ __forceinline__ uint32_t bucket_add(uint32_t* s, int b) {
+  const uint32_t peers = __match_any_sync(0xffffffffu, b);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (b >= 0 && lane == leader) base = atomicAdd(s + b, (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+// The tiles in the order the blend kernels take them.  Where lists are long
+// on average, by list length, longest first (to a quarter octave; the order
+// within a bucket is arbitrary), so that long tiles start early and do not
+// trail the grid; where they are short, the blend kernels keep the tiles'
+// own order (neighbouring tiles share records) and nothing here runs.
+// Every tile appears once, so the order changes no result.
+//
+// Up to kOrdSingle tiles: one block counts the tiles per bucket, scans the
+// counts and places the tiles.
+constexpr uint32_t kOrdSingle = 16384;
+__global__ void __launch_bounds__(kOrdT) tile_order_single_kernel(const uint32_t* __restrict__ tstart, uint32_t NT,
+                                                                 uint32_t cap, const Header* hdr,
+                                                                 uint32_t* __restrict__ order) {
+  wait_prior_grid();
+  if (!order_dense(hdr, NT, cap)) return;
+  __shared__ uint32_t s_n[kOrdBuckets];
+  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT) s_n[i] = 0;
+  __syncthreads();
+  const uint32_t rounds = (NT + kOrdT - 1) / kOrdT;  // the same for every thread: whole warps in bucket_add
+  for (uint32_t k = 0; k < rounds; ++k) {
+    const uint32_t t = k * kOrdT + threadIdx.x;
+    bucket_add(s_n, t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the counts: five buckets a lane
+    constexpr int PER = (kOrdBuckets + 31) / 32;
+    const int lane = threadIdx.x;
+    uint32_t c[PER], sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = lane * PER + j;
+      c[j] = i < kOrdBuckets ? s_n[i] : 0u;
+      sum += c[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = lane * PER + j;
+      if (i < kOrdBuckets) s_n[i] = run;
+      run += c[j];
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = 0; k < rounds; ++k) {
+    const uint32_t t = k * kOrdT + threadIdx.x;
+    const int b = t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1;
+    const uint32_t pos = bucket_add(s_n, b);
+    if (b >= 0) order[pos] = t;
+  }
+}
+
+// More tiles, pass 1: the tiles per bucket, one block per kOrdT tiles.
+__global__ void __launch_bounds__(kOrdT) tile_order_count_kernel(const uint32_t* __restrict__ tstart, uint32_t NT,
+                                                                uint32_t cap, const Header* hdr,
+                                                                uint32_t* __restrict__ totals) {
+  wait_prior_grid();
+  if (!order_dense(hdr, NT, cap)) return;
+  __shared__ uint32_t s_n[kOrdBuckets];
+  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT) s_n[i] = 0;
+  __syncthreads();
+  const uint32_t t = blockIdx.x * kOrdT + threadIdx.x;
+  bucket_add(s_n, t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT)
+    if (s_n[i]) atomicAdd(totals + i, s_n[i]);
+}
+
+// Pass 2: each block reserves a range per bucket (after the longer buckets'
+// totals) and places its tiles there.
+__global__ void __launch_bounds__(kOrdT) tile_order_place_kernel(const uint32_t* __restrict__ tstart, uint32_t NT,
+                                                                uint32_t cap, const Header* hdr,
+                                                                const uint32_t* __restrict__ totals,
+                                                                uint32_t* __restrict__ cursor,
+                                                                uint32_t* __restrict__ order) {
+  wait_prior_grid();
+  if (!order_dense(hdr, NT, cap)) return;
+  const uint32_t t = blockIdx.x * kOrdT + threadIdx.x;
+  __shared__ uint32_t s_n[kOrdBuckets], s_base[kOrdBuckets];
+  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT) s_n[i] = 0;
+  __syncthreads();
+  const int b = t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1;
+  const uint32_t rank = bucket_add(s_n, b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t start = 0;  // the bucket's first position: the longer buckets' totals
+    for (int i = 0; i < kOrdBuckets; ++i) {
+      if (s_n[i]) s_base[i] = start + atomicAdd(cursor + i, s_n[i]);
+      start += totals[i];
+    }
+  }
+  __syncthreads();
+  if (b >= 0) order[s_base[b] + rank] = t;
+}
+
 }  // namespace
 
 const uint32_t* sorted_instances(const Layout& L, const char* ws) {
@@ -472,10 +597,27 @@ const uint32_t* sorted_instances(const Layout& L, const char* ws) {
 // kernels; each loops over the blocks of work the device counts call for
 constexpr uint32_t kPassGrid = 152 * 4, kEmitGrid = 152 * 8;
 
+cudaError_t launch_tile_order(const Layout& L, char* ws, const Header* hdr, cudaStream_t st) {
+  if (!order_possible(L)) return cudaSuccess;  // the lists cannot be dense: the tiles keep their order
+  const uint32_t* tstart = (const uint32_t*)(ws + L.tstart);
+  uint32_t* order = (uint32_t*)(ws + L.tile_order);
+  if (L.NT <= kOrdSingle) {
+    launch_dependent(tile_order_single_kernel, dim3(1), dim3(kOrdT), 0, st, tstart, L.NT, L.cap, hdr, order);
+    return cudaGetLastError();
+  }
+  uint32_t* totals = (uint32_t*)(ws + L.order_count);  // zeroed at the start of bin_sort
+  const unsigned blocks = (L.NT + kOrdT - 1) / kOrdT;
+  launch_dependent(tile_order_count_kernel, dim3(blocks), dim3(kOrdT), 0, st, tstart, L.NT, L.cap, hdr, totals);
+  launch_dependent(tile_order_place_kernel, dim3(blocks), dim3(kOrdT), 0, st, tstart, L.NT, L.cap, hdr,
+                   (const uint32_t*)totals, totals + kOrdBuckets, order);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaStream_t st) {
   (void)cfg;
   Header* hdr = (Header*)(ws + L.header);
-  if (L.R == 0) return cudaMemsetAsync(ws + L.tstart, 0, (size_t)(L.NT + 1) * 4, st);
+  if (L.R == 0)  // no records: every list is empty (and the tiles keep their order)
+    return cudaMemsetAsync(ws + L.tstart, 0, (size_t)(L.NT + 1) * 4, st);
   // the per-pass counts are accumulated with atomics: start them at zero
   cudaError_t e = cudaMemsetAsync(ws + L.hist_d, 0, L.Tfin - L.hist_d, st);
   if (e != cudaSuccess) return e;
@@ -534,7 +676,7 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   }
   const uint32_t* skeys = (const uint32_t*)(ws + ((L.tile_passes & 1) ? L.ikB : L.ikA));
   launch_dependent(ranges_kernel, dim3(592), dim3(256), 0, st, skeys, &hdr->n_inst, L.cap, L.NT, (uint32_t*)(ws + L.tstart));
-  return cudaGetLastError();
+  return launch_tile_order(L, ws, hdr, st);
 }
 
 void sort_tile_sizes(uint32_t R, uint32_t cap, uint32_t* n_cmp, uint32_t* n_emit, uint32_t* n_dsort,
