@@ -200,9 +200,10 @@ def kernels_per_step(r):
     pre = upload + S
     # scan, compact, 4 depth passes (scan + downsweep), scan, emission offsets
     # and fill, tile-key passes (scan + downsweep), ranges, then the tile order
-    # where the capacity allows dense lists (one kernel up to 16384 tiles)
-    order = 0 if r.capacity < 64 * NT else (1 if NT <= 16384 else 2)
-    sort = 2 + 4 * 2 + 3 + 2 * tile_passes + order
+    # over 1024 tiles where the capacity allows dense lists (one kernel up to
+    # 16384 tiles)
+    order = 0 if (NT <= 1024 or r.capacity < 64 * NT) else (1 if NT <= 16384 else 2)
+    sort = 2 + 4 * 2 + 3 + 2 * tile_passes + 1 + order
     # forward blend; zeroing of the visible records' gradient sums, backward
     # blend; parameter backward per scene
     return pre + sort + 1 + 2 + S

@@ -24,9 +24,14 @@ __device__ __forceinline__ bool order_dense(const Header* hdr, uint32_t NT, uint
   const uint64_t n = hdr->n_inst < cap ? hdr->n_inst : cap;
   return n >= (uint64_t)kOrdDense * NT;
 }
-// whether the lists can be dense at all with the layout's instance capacity:
-// where not, no order is made and the blend kernels get none
-inline bool order_possible(const Layout& L) { return (uint64_t)L.cap >= (uint64_t)kOrdDense * L.NT; }
+// whether an order can pay at all: more tiles than a few waves of blend
+// CTAs (with fewer, every tile starts at once) and an instance capacity that
+// allows dense lists; where not, no order is made and the blend kernels get
+// none
+constexpr uint32_t kOrdMinTiles = 1024;
+inline bool order_possible(const Layout& L) {
+  return L.NT > kOrdMinTiles && (uint64_t)L.cap >= (uint64_t)kOrdDense * L.NT;
+}
 
 template <typename... Params, typename... Args>
 cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -104,13 +104,21 @@ __device__ __forceinline__ void eval_pair(float lx, float ly, const float4& p, c
   e.use = (e.r < 1.0f) && (e.alpha >= amin);
 }
 
-__device__ __forceinline__ int find_view(const ViewDev* __restrict__ views, int V, uint32_t g) {
-  int lo = 0, hi = V - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (views[mid].tile_off <= g) lo = mid; else hi = mid - 1;
+// The view holding global tile g: the last view whose first tile is at or
+// before g (views are numbered in tile order and view 0 starts at tile 0).
+// Called by a whole warp: a ballot over 32 views, after one over the first
+// views of 32-view chunks when there are more than 32 -- at most two
+// dependent loads, where a binary search takes log2(V).
+__device__ __forceinline__ int find_view_warp(const ViewDev* __restrict__ views, int V, uint32_t g) {
+  if (V == 1) return 0;
+  const int lane = threadIdx.x & 31;
+  int c = 0;
+  if (V > 32) {
+    const int i = lane * 32;
+    c = 31 - __clz(__ballot_sync(kFull, i < V && views[i].tile_off <= g));
   }
-  return lo;
+  const int i = c * 32 + lane;
+  return c * 32 + (31 - __clz(__ballot_sync(kFull, i < V && views[i].tile_off <= g)));
 }
 
 // the warp's 8 x RB block (bx, by) within a TW-wide tile and this lane's
@@ -189,7 +197,11 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
   // the tile order where there is one (long lists on average): the header
   // is at hand already, the order costs one more dependent load
   const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x] : blockIdx.x;
-  if (threadIdx.x == 0) s_v = find_view(views, V, g);
+  const uint32_t start = tstart[g], end = tstart[g + 1];  // loaded while warp 0 finds the view
+  if (threadIdx.x < 32) {
+    const int vi = find_view_warp(views, V, g);
+    if (threadIdx.x == 0) s_v = vi;
+  }
   __syncthreads();
   const ViewDev& v = views[s_v];
   const uint32_t lt = g - v.tile_off;
@@ -203,7 +215,6 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
   const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 3.0f;
   const float lg2_amin = lg2_approx(cfg.amin);
   uint8_t* list = s_list[threadIdx.x >> 5];
-  const uint32_t start = tstart[g], end = tstart[g + 1];
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
   uint32_t last = 0, np = 0;
   bool done = !inside;
@@ -366,7 +377,8 @@ __global__ void __launch_bounds__(32)
   const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x / BPT] : blockIdx.x / BPT;
   const int wb = blockIdx.x % BPT;
   const int lane = threadIdx.x;
-  const ViewDev& v = views[find_view(views, V, g)];
+  const uint32_t start = tstart[g];  // loaded while the view is found
+  const ViewDev& v = views[find_view_warp(views, V, g)];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
   const int bx = (wb % WPR) * 8, by = (wb / WPR) * 8;
@@ -404,7 +416,6 @@ __global__ void __launch_bounds__(32)
   const float ox = (float)(tx * TW), oy = (float)(ty * TH);
   const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 7.0f;
   const float lg2_amin = lg2_approx(cfg.amin);
-  const uint32_t start = tstart[g];
   const int wslot = writer_of(lane);
   for (int hi = (int)wlast; hi > 0; hi -= WB) {
     const int lo = hi - WB > 0 ? hi - WB : 0;

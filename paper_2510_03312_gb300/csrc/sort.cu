@@ -83,7 +83,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total,
 
 // ---------------------------------------------------------------- column scan
 
-constexpr int kScT = 256, kScI = 4;
+constexpr int kScT = 256, kScI = 8;
 
 // Exclusive scan down each column of a row-major [rows][cols] matrix (out
 // may equal in); one block per column; the column sums go to totals (if
@@ -477,8 +477,17 @@ __device__ __forceinline__ int length_bucket(uint32_t n) {
 // Warp-aggregated add of 1 to s[b] (b < 0: no add): the lanes sharing a
 // bucket make one shared-memory atomic, and each gets its rank among the
 // lanes that came before it in the warp; returns the old value plus the rank.
+// The lanes sharing the bucket are found with one ballot per bit of it.
+static_assert(kOrdBuckets < 255, "bucket ids and the no-bucket id fit 8 bits");
 __device__ __forceinline__ uint32_t bucket_add(uint32_t* s, int b) {
-  const uint32_t peers = __match_any_sync(0xffffffffu, b);
+  const uint32_t key = b >= 0 ? (uint32_t)b : 255u;
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int bit = 0; bit < 8; ++bit) {
+    const bool one = (key >> bit) & 1u;
+    const uint32_t m = __ballot_sync(0xffffffffu, one);
+    peers &= one ? m : ~m;
+  }
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
   uint32_t base = 0;
@@ -505,11 +514,17 @@ __global__ void __launch_bounds__(kOrdT) tile_order_single_kernel(const uint32_t
   __shared__ uint32_t s_n[kOrdBuckets];
   for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT) s_n[i] = 0;
   __syncthreads();
-  const uint32_t rounds = (NT + kOrdT - 1) / kOrdT;  // the same for every thread: whole warps in bucket_add
-  for (uint32_t k = 0; k < rounds; ++k) {
+  // every tile's bucket in registers first: the loads are all in flight at once
+  constexpr int PER_T = kOrdSingle / kOrdT;
+  int bk[PER_T];
+#pragma unroll
+  for (int k = 0; k < PER_T; ++k) {
     const uint32_t t = k * kOrdT + threadIdx.x;
-    bucket_add(s_n, t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1);
+    bk[k] = t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1;
   }
+#pragma unroll
+  for (int k = 0; k < PER_T; ++k)
+    if (k * kOrdT < NT) bucket_add(s_n, bk[k]);  // uniform over the block: whole warps
   __syncthreads();
   if (threadIdx.x < 32) {  // exclusive scan of the counts: five buckets a lane
     constexpr int PER = (kOrdBuckets + 31) / 32;
@@ -536,12 +551,12 @@ __global__ void __launch_bounds__(kOrdT) tile_order_single_kernel(const uint32_t
     }
   }
   __syncthreads();
-  for (uint32_t k = 0; k < rounds; ++k) {
-    const uint32_t t = k * kOrdT + threadIdx.x;
-    const int b = t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1;
-    const uint32_t pos = bucket_add(s_n, b);
-    if (b >= 0) order[pos] = t;
-  }
+#pragma unroll
+  for (int k = 0; k < PER_T; ++k)
+    if (k * kOrdT < NT) {
+      const uint32_t pos = bucket_add(s_n, bk[k]);
+      if (bk[k] >= 0) order[pos] = k * kOrdT + threadIdx.x;
+    }
 }
 
 // More tiles, pass 1: the tiles per bucket, one block per kOrdT tiles.
