@@ -98,9 +98,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList v
 // values as in view_stage.
 constexpr int kQCap = 64;   // queue entries per warp: 31 carried over + 32 new
 constexpr int kQWarps = 8;  // warps per CTA (256 threads)
+// Held to 80 registers (three CTAs per SM, from two at 108-116): the
+// kernel's dependent float32 chains need the warps (the 16-view N=6 batch
+// 253 -> 232 us, the 8-view N=7 one 99 -> 91 us).
 
 template <int C>
-__global__ void __launch_bounds__(256) preprocess_queued_kernel(SceneDev sc, ViewList vl,
+__global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, ViewList vl,
                                                                 const ViewDev* __restrict__ views, CfgDev cfg,
                                                                 float4* __restrict__ rec4, uint32_t* __restrict__ key,
                                                                 uint32_t* __restrict__ tiles, uint2* __restrict__ rect,

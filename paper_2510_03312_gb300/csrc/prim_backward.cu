@@ -100,9 +100,12 @@ __global__ void __launch_bounds__(256) zero_scene_grads_kernel(SceneGradDev gr, 
 // however sparse the visibility; the other primitives keep the zeros of
 // zero_scene_grads_kernel (or their sum, when accumulating).  Each lane walks
 // only its own visible views (a bit mask per 32 views), so a warp runs as
-// many per-view steps as its busiest lane needs.
+// many per-view steps as its busiest lane needs.  The C = 3 instantiation
+// (216 registers unbounded) is held to 128 so that four CTAs share an SM: it
+// is bound by memory latency, and the occupancy outweighs its spills (the
+// 16-view N=6 batch 135 -> 122 us); the C = 4 one lost time that way.
 template <int C>
-__global__ void __launch_bounds__(128) prim_backward_listed_kernel(SceneDev sc, SceneGradDev gr, ViewList vl,
+__global__ void __launch_bounds__(128, C == 3 ? 4 : 1) prim_backward_listed_kernel(SceneDev sc, SceneGradDev gr, ViewList vl,
                                                             const ViewDev* __restrict__ views, CfgDev cfg,
                                                             const uint32_t* __restrict__ tiles,
                                                             const float4* __restrict__ g2d,
