@@ -231,3 +231,36 @@ def test_full_size_static_sampled():
     worst, nflag, ref = check_images(gpu, orc, recs=recs, tiles=tiles)
     print(f"full size: max image error {worst:.2e} on {len(tiles)} tiles, flagged {nflag}")
     check_grads(gpu, orc, ref, tiles=tiles)
+
+
+def test_empty_scenes():
+    """A problem whose only scene has no primitives (no records at all)
+    renders the background with nothing to sort; beside a non-empty scene,
+    an empty one changes nothing of the other scene's view, and its
+    gradient is empty."""
+    from paper_2510_03312_gb300 import raster
+    K = S.params_per_primitive(3, S.ROT_QUAT)
+    empty = S.Scene(3, S.ROT_QUAT, np.zeros((K, 0), np.float32))
+    R, t = S.look_at((0.0, 0.0, -3.0))
+    cfg = S.RasterConfig(bg=(0.25, 0.5, 0.75))
+    gpu = gpu_forward([empty], [S.make_view(R, t, 40, 24)], cfg)
+    assert gpu["status"].status == 0 and gpu["status"].instances == 0
+    for c, b in enumerate(cfg.bg):
+        assert np.all(gpu["images"][0][c] == np.float32(b))
+    # an empty scene beside a non-empty one
+    full = S.make_scene(51, 3, 800, means="uniform", extent=1.0)
+    v_full = S.make_view(R, t, 72, 56, scene_id=1)
+    v_empty = S.make_view(R, t, 40, 24, scene_id=0)
+    both = gpu_forward([empty, full], [v_empty, v_full], cfg)
+    alone = gpu_forward([full], [S.make_view(R, t, 72, 56)], cfg)
+    assert both["status"].status == 0
+    assert np.array_equal(both["images"][1], alone["images"][0])
+    for c, b in enumerate(cfg.bg):
+        assert np.all(both["images"][0][c] == np.float32(b))
+    rng = np.random.default_rng(2)
+    dl = torch.from_numpy(rng.uniform(-1, 1, both["image_flat"].numel()).astype(np.float32)).cuda()
+    r = both["rast"]
+    r.forward(check=False)
+    g = r.backward(dl.view_as(both["image_flat"]))
+    torch.cuda.synchronize()
+    assert g[0].numel() == 0 and torch.isfinite(g[1]).all() and float(g[1].abs().max()) > 0
