@@ -404,7 +404,7 @@ def bench_ours(args, rank, world, local):
         "wall_s_timed_loop": round(wall, 3),
     }
     if rank == 0 and not args.no_batched and world == 1:
-        out["batched"] = bench_batched(dev)
+        out["batched"] = bench_batched(dev, pk, n_sm)
         out["forward_only"] = bench_small_forward(dev)
     if dist:
         dist.destroy_process_group()
@@ -532,7 +532,49 @@ def bench_small_forward(dev, steps=200, warmup=20):
     return {wl.name: out}
 
 
-def bench_batched(dev, steps=5, warmup=2):
+def batched_rooflines(ds, wl, dev, pk, n_sm, steps, warmup):
+    """Roofline of one batch: the whole batch as one problem (16x16 tiles),
+    each stage timed with CUDA events, against the same per-unit work as the
+    single view's stages (parameters read once per batch).  Also returns
+    the parameter bytes of the batch and of the per-view form (which reads a
+    scene's parameters once per view, in preprocess and twice in the
+    parameter backward)."""
+    import torch
+
+    from paper_2510_03312_gb300 import raster
+
+    r = raster.Rasterizer(ds, wl.views, wl.cfg, device=dev)
+    img = r.forward(check=True)
+    st = r.status()
+    r.problem.cfg.flags |= 2
+    r.render_fwd()
+    pairs = int(r.export(9).to(torch.int64).sum().item())
+    r.problem.cfg.flags &= ~2
+    dL = torch.full_like(img, 1e-6)
+    names = ["preprocess", "bin_sort", "render_fwd", "render_bwd_blend", "render_bwd_params"]
+    stream = torch.cuda.current_stream()
+    calls = [r.preprocess, r.bin_sort, r.render_fwd, lambda: r.render_bwd_blend(dL), r.render_bwd_params]
+    rows = []
+    for i in range(warmup + steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        evs[0].record(stream)
+        for k, c in enumerate(calls):
+            c()
+            evs[k + 1].record(stream)
+        if i >= warmup:
+            rows.append(evs)
+    torch.cuda.synchronize()
+    stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(5)] for e in rows]).mean(0)
+    batch_pb = sum(d.params.numel() * 4 for d in ds)
+    view_pb = sum(ds[v.scene_id].params.numel() * 4 for v in wl.views)
+    R = sum(ds[v.scene_id].P for v in wl.views)
+    steps_roof, path = step_rooflines(stage, names, batch_pb, R, int(st.instances), r.n_tiles(), pairs, pk, n_sm)
+    del r
+    torch.cuda.empty_cache()
+    return steps_roof, path, batch_pb, view_pb, pairs
+
+
+def bench_batched(dev, pk, n_sm, steps=5, warmup=2):
     """Batches of views, forward+backward per step:
       view-dependent N=6, 500K primitives, 16 x 1280x720;
       dynamic N=7, 300K primitives, 8 (camera, time) x 1352x1014;
@@ -542,7 +584,10 @@ def bench_batched(dev, steps=5, warmup=2):
     form); batched_one_launch = all views in one problem, 16x16 tiles, eager;
     batched = the autotuned tile shape and schedule with the whole step
     replayed as one captured CUDA graph.  Gradients of each scene are summed
-    over its views in every form."""
+    over its views in every form.  Each form's roofline fraction is
+    t_roof / t_step, t_roof the time of the form's algorithmic work at the
+    peaks (batched_rooflines; the per-view form adds its extra parameter
+    reads; the autotuned form is counted at 16x16 tiles)."""
     import torch
 
     from paper_2510_03312_gb300 import autotune as A
@@ -583,8 +628,18 @@ def bench_batched(dev, steps=5, warmup=2):
                                "launches": len(plan.groups), "captured_graph": True})
         out["autotune"] = {"seconds": round(t_tune, 1), "candidates_ms": plan.table}
         out["speedup_batched"] = round(out["per_view"]["ms_per_step"] / out["batched"]["ms_per_step"], 3)
+        del b, dls, g
+        torch.cuda.empty_cache()
+        steps_roof, path, batch_pb, view_pb, pairs = batched_rooflines(ds, wl, dev, pk, n_sm, steps, warmup)
+        t_roof = path["t_roof_ms"]
+        t_roof_pv = t_roof + 3 * (view_pb - batch_pb) / (pk["hbm_gbs"] * 1e9) * 1e3
+        out["pairs"] = pairs
+        out["roofline_steps"] = steps_roof
+        out["roofline_path"] = path
+        for form, tr in (("per_view", t_roof_pv), ("batched_one_launch", t_roof), ("batched", t_roof)):
+            out[form]["roofline_frac"] = round(tr / out[form]["ms_per_step"], 4)
         res[wl.name] = out
-        del b, dls, g, ds
+        del ds
         torch.cuda.empty_cache()
     return res
 

@@ -377,8 +377,10 @@ __global__ void __launch_bounds__(32)
   const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x / BPT] : blockIdx.x / BPT;
   const int wb = blockIdx.x % BPT;
   const int lane = threadIdx.x;
-  const uint32_t start = tstart[g];  // loaded while the view is found
-  const ViewDev& v = views[find_view_warp(views, V, g)];
+  const uint32_t start = tstart[g], end = tstart[g + 1];  // loaded while the view is found
+  const int vi = find_view_warp(views, V, g);
+  if (start == end) return;  // an empty list: no pixel of the tile has a contributor
+  const ViewDev& v = views[vi];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
   const int bx = (wb % WPR) * 8, by = (wb / WPR) * 8;
