@@ -192,7 +192,7 @@ constexpr int kOsT = 256, kOsW = kOsT / 32;
 // The counts are summed over lanes with equal (block, digit) before one
 // atomic add per group.  A block ranks TILE items.
 template <int TILE>
-__global__ void __launch_bounds__(kOsT) downsweep_kernel(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(kOsT, 5) downsweep_kernel(const uint32_t* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                                                          uint32_t* __restrict__ vout, const uint64_t* n_ptr,
                                                          uint32_t cap, int shift, const uint32_t* __restrict__ ghist,
@@ -608,9 +608,11 @@ const uint32_t* sorted_instances(const Layout& L, const char* ws) {
   return (const uint32_t*)(ws + ((L.tile_passes & 1) ? L.ivB : L.ivA));
 }
 
-// grids of the radix passes (4 resident CTAs per SM) and of the emission
-// kernels; each loops over the blocks of work the device counts call for
-constexpr uint32_t kPassGrid = 152 * 4, kEmitGrid = 152 * 8;
+// grids of the radix passes (5 resident CTAs per SM: the pass is held to 48
+// registers for it, against 4 CTAs at 64 -- the 64-job mix's sort 1676 ->
+// 1622 us; 6 spilled) and of the emission kernels; each loops over the
+// blocks of work the device counts call for
+constexpr uint32_t kPassGrid = 152 * 5, kEmitGrid = 152 * 8;
 
 cudaError_t launch_tile_order(const Layout& L, char* ws, const Header* hdr, cudaStream_t st) {
   if (!order_possible(L)) return cudaSuccess;  // the lists cannot be dense: the tiles keep their order
