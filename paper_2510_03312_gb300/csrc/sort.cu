@@ -336,6 +336,8 @@ __global__ void __launch_bounds__(kEmT) emit_offsets_kernel(const uint32_t* __re
 }
 
 constexpr int kFlT = 256, kFlI = kIsTile / kFlT;
+static_assert(kFlI == 8, "a thread's instances are written as two 16-byte vectors per array");
+static_assert(kMaxViews <= 256, "view indices are staged as bytes");
 
 // Instances [b K, (b + 1) K) of the depth-sorted order, K = kIsTile: block b
 // of the first tile-key pass, so that every block does the same work however
@@ -343,8 +345,11 @@ constexpr int kFlT = 256, kFlI = kIsTile / kFlT;
 // sorted record i with ioff[i] <= j < ioff[i + 1] and is that record's
 // (j - ioff[i])-th tile, row-major in its rectangle; it is written as
 // (global tile, record).  ioff strictly increases (every visible record
-// touches a tile), so the records holding the block's instances are the K
-// from the one holding its first instance on.  Writes the first tile pass's
+// touches a tile), so the block's instances lie in at most K records from
+// the one holding its first instance.  The block first stages those
+// records (id, rectangle, view) in shared memory, all gathers in flight at
+// once; each thread then walks its kFlI consecutive instances from shared
+// memory and writes them as 16-byte vectors.  Writes the first tile pass's
 // digit counts of the block.
 __global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restrict__ srec,
                                                          const uint32_t* __restrict__ ioff,
@@ -354,22 +359,26 @@ __global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restr
                                                          uint32_t* __restrict__ hist0, const Header* hdr) {
   wait_prior_grid();
   __shared__ uint32_t s_off[kIsTile + 1];
+  __shared__ uint32_t s_rec[kIsTile];
+  __shared__ uint2 s_rect[kIsTile];
+  __shared__ uint8_t s_view[kIsTile];
   __shared__ uint32_t s_h[256];
   __shared__ uint32_t s_recoff[kMaxViews], s_tileoff[kMaxViews], s_tilesx[kMaxViews];
-  __shared__ uint32_t s_r0;
+  __shared__ uint32_t s_r0, s_nr;
   const uint32_t nv = (uint32_t)hdr->n_visible;
   const uint64_t ni64 = hdr->n_inst;
   const uint32_t n_inst = (uint32_t)(ni64 < cap ? ni64 : cap);
   if (nv == 0) return;
+  for (int i = threadIdx.x; i < V; i += kFlT) {
+    s_recoff[i] = views[i].rec_off;
+    s_tileoff[i] = views[i].tile_off;
+    s_tilesx[i] = (uint32_t)views[i].tiles_x;
+  }
   for (uint32_t b = blockIdx.x; (uint64_t)b * kIsTile < n_inst; b += gridDim.x) {
     const uint32_t s = b * kIsTile;
     __syncthreads();  // the shared arrays of the previous block are free
     for (int i = threadIdx.x; i < 256; i += kFlT) s_h[i] = 0;
-    for (int i = threadIdx.x; i < V; i += kFlT) {
-      s_recoff[i] = views[i].rec_off;
-      s_tileoff[i] = views[i].tile_off;
-      s_tilesx[i] = (uint32_t)views[i].tiles_x;
-    }
+    if (threadIdx.x == 0) s_nr = 0;
     if (threadIdx.x < 32) {
       // the last sorted record with ioff <= s, by a 32-way search: each round
       // samples 32 offsets of [lo, hi) and keeps the span after the last one
@@ -389,52 +398,105 @@ __global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restr
     }
     __syncthreads();
     const uint32_t r0 = s_r0;
-    for (uint32_t i = threadIdx.x; i <= (uint32_t)kIsTile; i += kFlT)
-      s_off[i] = r0 + i < nv ? ioff[r0 + i] : 0xffffffffu;
+    // the offsets of records r0 .. r0 + K, and the number of those records
+    // that start inside the block (the records holding its instances)
+    uint32_t starts = 0;
+    for (uint32_t i = threadIdx.x; i <= (uint32_t)kIsTile; i += kFlT) {
+      const uint32_t o = r0 + i < nv ? ioff[r0 + i] : 0xffffffffu;
+      s_off[i] = o;
+      starts += (i < (uint32_t)kIsTile && o < s + (uint32_t)kIsTile);
+    }
+    if (starts) atomicAdd(&s_nr, starts);
     __syncthreads();
-    // kFlI consecutive instances per thread, walking the records
+    const uint32_t nr = min(s_nr, (uint32_t)kIsTile);
+    // stage those records (id, rectangle and view), a thread's ids loaded
+    // together and then its rectangles
+    {
+      uint32_t rk[kFlI];
+      uint2 rc[kFlI];
+#pragma unroll
+      for (int k = 0; k < kFlI; ++k) {
+        const uint32_t i = threadIdx.x + k * kFlT;
+        rk[k] = i < nr ? srec[r0 + i] : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < kFlI; ++k) {
+        const uint32_t i = threadIdx.x + k * kFlT;
+        if (i < nr) rc[k] = rect[rk[k]];
+      }
+#pragma unroll
+      for (int k = 0; k < kFlI; ++k) {
+        const uint32_t i = threadIdx.x + k * kFlT;
+        if (i < nr) {
+          int vlo = 0, vhi = V - 1;  // view of the record: last view with rec_off <= rec
+          while (vlo < vhi) {
+            const int mid = (vlo + vhi + 1) >> 1;
+            if (s_recoff[mid] <= rk[k]) vlo = mid; else vhi = mid - 1;
+          }
+          s_rec[i] = rk[k];
+          s_rect[i] = rc[k];
+          s_view[i] = (uint8_t)vlo;
+        }
+      }
+    }
+    __syncthreads();
+    // kFlI consecutive instances per thread, walking the staged records
     const uint32_t j0 = s + threadIdx.x * kFlI;
     if (j0 < n_inst) {
-      int lo = 0, hi = kIsTile - 1;  // last i with s_off[i] <= j0 (s_off[0] <= s, s_off[K] > s + K - 1)
+      int lo = 0, hi = (int)nr - 1;  // last i with s_off[i] <= j0 (s_off[0] <= s)
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (s_off[mid] <= j0) lo = mid; else hi = mid - 1;
       }
       uint32_t i = (uint32_t)lo;
+      uint32_t kk[kFlI], vv[kFlI];
       uint32_t rec = 0, x0 = 0, x1 = 0, tx = 0, ty = 0, vt = 0, vx = 0;
       bool fresh = true;
+#pragma unroll
       for (int k = 0; k < kFlI; ++k) {
         const uint32_t j = j0 + k;
-        if (j >= n_inst) break;
-        while (s_off[i + 1] <= j) {  // stays below K: s_off[K] > j
-          ++i;
-          fresh = true;
-        }
-        if (fresh) {
-          fresh = false;
-          rec = srec[r0 + i];
-          const uint2 rc = rect[rec];
-          x0 = rc.x & 0xFFFFu;
-          x1 = rc.y & 0xFFFFu;
-          const uint32_t w = x1 - x0, local = j - s_off[i];
-          tx = x0 + local % w;
-          ty = (rc.x >> 16) + local / w;
-          int vlo = 0, vhi = V - 1;  // view of the record: last view with rec_off <= rec
-          while (vlo < vhi) {
-            const int mid = (vlo + vhi + 1) >> 1;
-            if (s_recoff[mid] <= rec) vlo = mid; else vhi = mid - 1;
+        kk[k] = vv[k] = 0;
+        if (j < n_inst) {
+          while (s_off[i + 1] <= j) {  // stays below nr: s_off[nr] > j
+            ++i;
+            fresh = true;
           }
-          vt = s_tileoff[vlo];
-          vx = s_tilesx[vlo];
+          if (fresh) {
+            fresh = false;
+            rec = s_rec[i];
+            const uint2 rc = s_rect[i];
+            x0 = rc.x & 0xFFFFu;
+            x1 = rc.y & 0xFFFFu;
+            const uint32_t w = x1 - x0, local = j - s_off[i];
+            tx = x0 + local % w;
+            ty = (rc.x >> 16) + local / w;
+            vt = s_tileoff[s_view[i]];
+            vx = s_tilesx[s_view[i]];
+          }
+          const uint32_t gt = vt + ty * vx + tx;
+          kk[k] = gt;
+          vv[k] = rec;
+          atomicAdd(&s_h[gt & 255u], 1u);
+          if (++tx == x1) {
+            tx = x0;
+            ++ty;
+          }
         }
-        const uint32_t gt = vt + ty * vx + tx;
-        ikey[j] = gt;
-        ival[j] = rec;
-        atomicAdd(&s_h[gt & 255u], 1u);
-        if (++tx == x1) {
-          tx = x0;
-          ++ty;
-        }
+      }
+      if (j0 + kFlI <= n_inst) {  // j0 is a multiple of 8: 32-byte aligned
+        uint4* kd = reinterpret_cast<uint4*>(ikey + j0);
+        uint4* vd = reinterpret_cast<uint4*>(ival + j0);
+        kd[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
+        kd[1] = make_uint4(kk[4], kk[5], kk[6], kk[7]);
+        vd[0] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
+        vd[1] = make_uint4(vv[4], vv[5], vv[6], vv[7]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kFlI; ++k)
+          if (j0 + k < n_inst) {
+            ikey[j0 + k] = kk[k];
+            ival[j0 + k] = vv[k];
+          }
       }
     }
     __syncthreads();
