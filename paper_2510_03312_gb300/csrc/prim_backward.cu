@@ -29,11 +29,13 @@ __device__ __forceinline__ void load_prim_b(const SceneDev& sc, int64_t p, PrimI
   }
 }
 
-// N = 3 (C = 0) is held to 80 registers (6 CTAs per SM): G2 is bound by
+// N = 3 (C = 0) is held to 72 registers (7 CTAs per SM): G2 is bound by
 // memory latency and gains more from occupancy than it loses to a few spills
-// to L1; the larger query dimensions would spill too much
+// to L1 (63.5 us unbounded, 53.7 at 6 CTAs, 51.9 at 7 on the 1M-primitive
+// view; 8 gained nothing more); the larger query dimensions would spill too
+// much
 template <int C>
-__global__ void __launch_bounds__(128, C == 0 ? 6 : 1) prim_backward_kernel(SceneDev sc, SceneGradDev gr, ViewList vl,
+__global__ void __launch_bounds__(128, C == 0 ? 7 : 1) prim_backward_kernel(SceneDev sc, SceneGradDev gr, ViewList vl,
                                                             const ViewDev* __restrict__ views, CfgDev cfg,
                                                             const uint32_t* __restrict__ tiles,
                                                             const float4* __restrict__ g2d) {

@@ -89,16 +89,20 @@ struct PairEval {
 
 // the one definition of a pair's alpha and skip decision, shared by the
 // forward and backward kernels: (lx, ly) is the pixel centre relative to the
-// tile origin
+// tile origin.  HOLD keeps 1 - r above zero for the backward, which divides
+// by it; the forward skips that (a pair with r >= 1 is never used, whatever
+// its alpha), and for r < 1 both give the same values.
+template <bool HOLD>
 __device__ __forceinline__ void eval_pair(float lx, float ly, const float4& p, const float4& q, float amin,
                                           float amax, PairEval& e) {
   e.dx = __fsub_rn(lx, p.x);
   e.dy = __fsub_rn(ly, p.y);
   const float t = __fmaf_rn(p.z, e.dx, __fmul_rn(p.w, e.dy));
   e.r = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(q.x, e.dy), e.dy));
-  // 1 - r, held above 0: a pair with r < 1 has 1 - r >= 2^-24 and is
-  // unchanged; for the others (never composited) log2 and 1/(1 - r) stay finite
-  e.om = fmaxf(__fsub_rn(1.0f, e.r), 1.0e-30f);
+  // 1 - r, held above 0 with HOLD: a pair with r < 1 has 1 - r >= 2^-24
+  // and is unchanged; for the others (never composited) log2 and
+  // 1/(1 - r) stay finite
+  e.om = HOLD ? fmaxf(__fsub_rn(1.0f, e.r), 1.0e-30f) : __fsub_rn(1.0f, e.r);
   e.lg = lg2_approx(e.om);
   e.alpha = fminf(amax, ex2_approx(__fmaf_rn(q.z, e.lg, q.y)));
   e.use = (e.r < 1.0f) && (e.alpha >= amin);
@@ -244,8 +248,8 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
       const bool has1 = i + 1 < cnt;
       const int j1 = has1 ? list[i + 1] : j0;
       PairEval e0, e1;
-      eval_pair(fx, fy, s_p[j0], s_q[j0], cfg.amin, cfg.amax, e0);
-      eval_pair(fx, fy, s_p[j1], s_q[j1], cfg.amin, cfg.amax, e1);
+      eval_pair<false>(fx, fy, s_p[j0], s_q[j0], cfg.amin, cfg.amax, e0);
+      eval_pair<false>(fx, fy, s_p[j1], s_q[j1], cfg.amin, cfg.amax, e1);
       if constexpr (COUNT) np += (!done && e0.r < 1.0f);
       {
         const bool u = !done && e0.use;
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(32)
       bool use[2], any = false;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        eval_pair(fx, fy[k], p, q, cfg.amin, cfg.amax, e[k]);
+        eval_pair<true>(fx, fy[k], p, q, cfg.amin, cfg.amax, e[k]);
         use[k] = e[k].use && (uint32_t)(lo + j) < last[k];  // pairs the forward composited
         any = any || use[k];
       }
