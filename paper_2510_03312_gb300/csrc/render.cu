@@ -1,17 +1,19 @@
 // render.cu -- R1 (forward blend) and G1 (backward blend).
 //
-// Forward: one CTA per screen tile, each warp owning an 8x4 pixel block,
-// one pixel per lane.  Backward: one single-warp CTA per 8x8 block of a tile,
-// two pixels per lane (rows y and y + 4), which halves the per-entry warp
-// reductions.  (Two pixels per lane made the forward slower: its per-pixel
-// early termination then diverges within a lane.)  The tile's front-to-back
-// list (sorted record ids) is consumed in batches of up to 256 records: each
-// batch's 48-byte render records are staged in shared memory together with
-// a conservative screen box of each record's support (the ellipse
-// r <= r_cut, r_cut the radius beyond which alpha < alpha_min, widened by a
-// margin).  Each warp first lists the batch entries whose box meets its
-// block (32 boxes per ballot) and then walks only that list -- a cull that
-// can only drop pairs whose alpha is below alpha_min, so no decision changes.
+// Both kernels give each warp an 8x8 pixel block of a tile and each lane two
+// pixels of one column (rows y and y + 4).  The two pixels' state and
+// arithmetic are carried in packed float32 pairs (add/mul/fma .f32x2 of
+// sm_100 and later), so one instruction serves both pixels; each record
+// scalar the pair arithmetic needs is staged twice in shared memory to sit
+// in such a pair.  Forward: one CTA per screen tile.  The tile's
+// front-to-back list (sorted record ids) is consumed in batches of up to 256
+// records: each batch's 48-byte render records are staged in shared memory
+// together with a conservative screen box of each record's support (the
+// ellipse r <= r_cut, r_cut the radius beyond which alpha < alpha_min,
+// widened by a margin).  Each warp first lists the batch entries whose
+// support meets its block (32 boxes per ballot) and then walks only that
+// list -- a cull that can only drop pairs whose alpha is below alpha_min, so
+// no decision changes.  Backward: one single-warp CTA per 8x8 block.
 //
 // Per pair (Sec. 3, Eq. r; Sec. 4.3 final density), with the screen mean
 // staged relative to the tile origin o as m = (hi - o) + lo:
@@ -49,6 +51,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// Packed float32 pairs (sm_100 and later): one instruction rounds each half
+// exactly as the scalar operation would (round to nearest even).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+
 // A staged record, tile-relative: the screen mean is re-expressed relative to
 // the tile origin (hi - origin) + lo, exact for the subtraction and rounded
 // once, so that per pair dx = (pixel centre - origin) - mean costs one add.
@@ -82,30 +97,51 @@ __device__ __forceinline__ void stage_record(const float4* __restrict__ rec4, ui
   }
 }
 
-struct PairEval {
-  float dx, dy, r, om, lg, alpha;
-  bool use;
+// A staged record, each scalar the pair arithmetic needs held twice so that
+// one packed instruction serves a lane's two pixels (rows y and y + 4 of
+// its column): A = (-mx, -mx, -my, -my), Bc = (a, a, 2b, 2b),
+// Cc = (c, c, beta_x, beta_x), D = (log2 o(q), log2 o(q), red, red),
+// E = (green, green, blue, blue).
+struct Staged2 {
+  float4 A, Bc, Cc, D, E;
+};
+__device__ __forceinline__ Staged2 pack_staged(const Staged& st) {
+  Staged2 s;
+  s.A = make_float4(-st.p.x, -st.p.x, -st.p.y, -st.p.y);
+  s.Bc = make_float4(st.p.z, st.p.z, st.p.w, st.p.w);
+  s.Cc = make_float4(st.q.x, st.q.x, st.q.z, st.q.z);
+  s.D = make_float4(st.q.y, st.q.y, st.q.w, st.q.w);
+  s.E = make_float4(st.s.x, st.s.x, st.s.y, st.s.y);
+  return s;
+}
+
+struct PairEval2 {
+  float2 dx, dy, r, om, lg, alpha;
 };
 
-// the one definition of a pair's alpha and skip decision, shared by the
-// forward and backward kernels: (lx, ly) is the pixel centre relative to the
-// tile origin.  HOLD keeps 1 - r above zero for the backward, which divides
-// by it; the forward skips that (a pair with r >= 1 is never used, whatever
-// its alpha), and for r < 1 both give the same values.
+// The one definition of a pair's r and alpha, shared by the forward and
+// backward kernels, for a lane's two pixels at once: (lx, ly.x) and
+// (lx, ly.y), pixel centres relative to the tile origin (dx is the same for
+// both).  Each half of a packed operation rounds as the scalar one would
+// (x + (-m) is x - m; fma(r, -1, 1) is 1 - r).  A pair is used when r < 1 and
+// alpha >= alpha_min.  HOLD keeps 1 - r above zero for the backward, which
+// divides by it; the forward skips that (a pair with r >= 1 is never used,
+// whatever its alpha), and for r < 1 both give the same values.
 template <bool HOLD>
-__device__ __forceinline__ void eval_pair(float lx, float ly, const float4& p, const float4& q, float amin,
-                                          float amax, PairEval& e) {
-  e.dx = __fsub_rn(lx, p.x);
-  e.dy = __fsub_rn(ly, p.y);
-  const float t = __fmaf_rn(p.z, e.dx, __fmul_rn(p.w, e.dy));
-  e.r = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(q.x, e.dy), e.dy));
+__device__ __forceinline__ void eval_pair2(float2 lx, float2 ly, const float4& A, const float4& Bc,
+                                           const float4& Cc, const float4& D, float amax, PairEval2& e) {
+  e.dx = add2(lx, lo2(A));
+  e.dy = add2(ly, hi2(A));
+  const float2 t = fma2(lo2(Bc), e.dx, mul2(hi2(Bc), e.dy));
+  e.r = fma2(e.dx, t, mul2(mul2(lo2(Cc), e.dy), e.dy));
   // 1 - r, held above 0 with HOLD: a pair with r < 1 has 1 - r >= 2^-24
   // and is unchanged; for the others (never composited) log2 and
   // 1/(1 - r) stay finite
-  e.om = HOLD ? fmaxf(__fsub_rn(1.0f, e.r), 1.0e-30f) : __fsub_rn(1.0f, e.r);
-  e.lg = lg2_approx(e.om);
-  e.alpha = fminf(amax, ex2_approx(__fmaf_rn(q.z, e.lg, q.y)));
-  e.use = (e.r < 1.0f) && (e.alpha >= amin);
+  const float2 om = fma2(e.r, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+  e.om = HOLD ? make_float2(fmaxf(om.x, 1.0e-30f), fmaxf(om.y, 1.0e-30f)) : om;
+  e.lg = make_float2(lg2_approx(e.om.x), lg2_approx(e.om.y));
+  const float2 ex = fma2(hi2(Cc), e.lg, lo2(D));
+  e.alpha = make_float2(fminf(amax, ex2_approx(ex.x)), fminf(amax, ex2_approx(ex.y)));
 }
 
 // The view holding global tile g: the last view whose first tile is at or
@@ -161,18 +197,21 @@ __device__ __forceinline__ bool ellipse_hits(const float4& p, float c, float rcu
 }
 
 // Each warp lists, in order, the staged entries j < n whose support meets
-// its block (all of them when `all`): the box test, then the exact ellipse
-// test; returns the count.
-__device__ __forceinline__ int warp_cull_list(const float4* s_bb, const float4* s_p, const float4* s_q,
-                                              const float* s_rc, int n, bool all, float x0, float x1, float y0,
-                                              float y1, uint8_t* list) {
+// its block (all of them when `all`), from the packed staging of the
+// two-pixel kernels; returns the count.
+__device__ __forceinline__ int warp_cull_list2(const float4* s_bb, const float4* s_A, const float4* s_B,
+                                               const float4* s_C, const float* s_rc, int n, bool all, float x0,
+                                               float x1, float y0, float y1, uint8_t* list) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int cnt = 0;
   for (int k = 0; k < n; k += 32) {
     const int j = k + lane;
     bool hit = j < n && (all || box_hits(s_bb[j], x0, x1, y0, y1));
-    if (hit && !all) hit = ellipse_hits(s_p[j], s_q[j].x, s_rc[j], x0, x1, y0, y1);
+    if (hit && !all) {
+      const float4 A = s_A[j], Bc = s_B[j];
+      hit = ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), s_C[j].x, s_rc[j], x0, x1, y0, y1);
+    }
     const unsigned m = __ballot_sync(kFull, hit);
     if (hit) list[cnt + __popc(m & lt)] = (uint8_t)j;
     cnt += __popc(m);
@@ -181,25 +220,28 @@ __device__ __forceinline__ int warp_cull_list(const float4* s_bb, const float4* 
   return cnt;
 }
 
+// Forward blend: a CTA per tile, a warp per 8x8 block, two pixels per lane
+// (rows y and y + 4) carried in packed pairs, so that the pair evaluation
+// and the compositing update run once per entry for both pixels.  Each half
+// takes the operations of the scalar rule above in the same order.  The
+// warp walks its list two entries per step between checks that its 64
+// pixels are all done; the CTA stops loading batches once its tile's are.
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 8))
+__global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW * TH / 2) : 16))
     render_fwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       float* __restrict__ image, float* __restrict__ Tfin, uint32_t* __restrict__ lastc,
                       const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs,
                       const uint32_t* __restrict__ tile_order, uint32_t n_tiles, uint32_t cap) {
   wait_prior_grid();
-  constexpr int B = TW * TH;
-  constexpr int BS = B < 256 ? B : 256;  // records staged per batch
-  constexpr int NW = B / 32;
-  __shared__ float4 s_p[BS], s_q[BS], s_bb[BS];
-  __shared__ float2 s_s[BS];
+  constexpr int NT = TW * TH / 2;           // threads: two pixels each
+  constexpr int BS = NT < 256 ? NT : 256;  // records staged per batch
+  constexpr int NW = NT / 32;
+  __shared__ float4 s_A[BS], s_B[BS], s_C[BS], s_D[BS], s_E[BS], s_bb[BS];
   __shared__ float s_rc[BS];
   __shared__ uint8_t s_list[NW][BS];
   __shared__ int s_v;
   if (hdr->status != 0) return;
-  // the tile order where there is one (long lists on average): the header
-  // is at hand already, the order costs one more dependent load
   const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x] : blockIdx.x;
   const uint32_t start = tstart[g], end = tstart[g + 1];  // loaded while warp 0 finds the view
   if (threadIdx.x < 32) {
@@ -211,91 +253,96 @@ __global__ void __launch_bounds__(TW * TH, (TW * TH >= 256 ? 1280 / (TW * TH) : 
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
   int lx, ly, bx, by;
-  pixel_of<TW, 4>(lx, ly, bx, by);
-  const int x = tx * TW + lx, y = ty * TH + ly;
-  const bool inside = x < v.W && y < v.H;
+  pixel_of<TW, 8>(lx, ly, bx, by);
+  const int x = tx * TW + lx, y0 = ty * TH + ly, y1 = y0 + 4;
+  const bool in0 = x < v.W && y0 < v.H, in1 = x < v.W && y1 < v.H;
   const float ox = (float)(tx * TW), oy = (float)(ty * TH);
-  const float fx = (float)lx + 0.5f, fy = (float)ly + 0.5f;  // pixel centre, tile-relative
-  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 3.0f;
+  const float2 fx = make_float2((float)lx + 0.5f, (float)lx + 0.5f);  // pixel centres, tile-relative
+  const float2 fy = make_float2((float)ly + 0.5f, (float)(ly + 4) + 0.5f);
+  const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 7.0f;
   const float lg2_amin = lg2_approx(cfg.amin);
+  const float2 one = make_float2(1.0f, 1.0f), neg1 = make_float2(-1.0f, -1.0f);
   uint8_t* list = s_list[threadIdx.x >> 5];
-  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-  uint32_t last = 0, np = 0;
-  bool done = !inside;
+  float2 T = one, C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0;
+  uint32_t last0 = 0, last1 = 0, np0 = 0, np1 = 0;
+  bool done0 = !in0, done1 = !in1;
   for (uint32_t base = start; base < end; base += BS) {
-    if (__syncthreads_count(done) == B) break;
+    if (__syncthreads_count(done0 && done1) == NT) break;
     const uint32_t idx = base + threadIdx.x;
     if (threadIdx.x < BS && idx < end) {
       Staged st;
       float4 box;
       stage_record(rec4, min(ivals[idx], R - 1), ox, oy, lg2_amin, st, box, s_rc[threadIdx.x]);  // ids < R
-      s_p[threadIdx.x] = st.p;
-      s_q[threadIdx.x] = st.q;
-      s_s[threadIdx.x] = st.s;
+      const Staged2 s2 = pack_staged(st);
+      s_A[threadIdx.x] = s2.A;
+      s_B[threadIdx.x] = s2.Bc;
+      s_C[threadIdx.x] = s2.Cc;
+      s_D[threadIdx.x] = s2.D;
+      s_E[threadIdx.x] = s2.E;
       s_bb[threadIdx.x] = box;
     }
     __syncthreads();
     const int n = (int)min((uint32_t)BS, end - base);
     // the counting variant visits every pair with r < 1
-    const int cnt = warp_cull_list(s_bb, s_p, s_q, s_rc, n, COUNT, wx0, wx1, wy0, wy1, list);
+    const int cnt = warp_cull_list2(s_bb, s_A, s_B, s_C, s_rc, n, COUNT, wx0, wx1, wy0, wy1, list);
     const uint32_t rel = base - start;
+    // one entry for both pixels; branch-free: a pair that is skipped (or
+    // stops its pixel) adds c * 0 and keeps T, which leaves C and T exactly
+    auto blend = [&](int j) {
+      const float4 D = s_D[j];
+      PairEval2 e;
+      eval_pair2<false>(fx, fy, s_A[j], s_B[j], s_C[j], D, cfg.amax, e);
+      const float2 r = e.r;
+      const float al0 = e.alpha.x, al1 = e.alpha.y;
+      if constexpr (COUNT) {
+        np0 += (!done0 && r.x < 1.0f);
+        np1 += (!done1 && r.y < 1.0f);
+      }
+      const bool u0 = !done0 && r.x < 1.0f && al0 >= cfg.amin;
+      const bool u1 = !done1 && r.y < 1.0f && al1 >= cfg.amin;
+      const float2 a = make_float2(u0 ? al0 : 0.0f, u1 ? al1 : 0.0f);
+      const float2 Tn = mul2(T, fma2(a, neg1, one));
+      const bool term0 = u0 && Tn.x < cfg.tmin, term1 = u1 && Tn.y < cfg.tmin;
+      done0 = done0 || term0;
+      done1 = done1 || term1;
+      const bool ok0 = u0 && !term0, ok1 = u1 && !term1;
+      float2 w = mul2(a, T);
+      w.x = ok0 ? w.x : 0.0f;
+      w.y = ok1 ? w.y : 0.0f;
+      const float4 E = s_E[j];
+      C0 = fma2(hi2(D), w, C0);
+      C1 = fma2(lo2(E), w, C1);
+      C2 = fma2(hi2(E), w, C2);
+      T.x = ok0 ? Tn.x : T.x;
+      T.y = ok1 ? Tn.y : T.y;
+      last0 = ok0 ? rel + j + 1 : last0;
+      last1 = ok1 ? rel + j + 1 : last1;
+    };
     for (int i = 0; i < cnt; i += 2) {
-      if (__all_sync(kFull, done)) break;
-      // two entries evaluated independently, applied in order; the update is
-      // branch-free: a pair that is skipped (or stops the pixel) adds c * 0
-      // and keeps T, which leaves C and T exactly as they were
-      const int j0 = list[i];
-      const bool has1 = i + 1 < cnt;
-      const int j1 = has1 ? list[i + 1] : j0;
-      PairEval e0, e1;
-      eval_pair<false>(fx, fy, s_p[j0], s_q[j0], cfg.amin, cfg.amax, e0);
-      eval_pair<false>(fx, fy, s_p[j1], s_q[j1], cfg.amin, cfg.amax, e1);
-      if constexpr (COUNT) np += (!done && e0.r < 1.0f);
-      {
-        const bool u = !done && e0.use;
-        const float a = u ? e0.alpha : 0.0f;
-        const float Tn = T * (1.0f - a);
-        const bool term = u && Tn < cfg.tmin;
-        done = done || term;
-        const bool ok = u && !term;
-        const float w = ok ? a * T : 0.0f;
-        const float4 q = s_q[j0];
-        const float2 c2 = s_s[j0];
-        C0 = fmaf(q.w, w, C0);
-        C1 = fmaf(c2.x, w, C1);
-        C2 = fmaf(c2.y, w, C2);
-        T = ok ? Tn : T;
-        last = ok ? rel + j0 + 1 : last;
-      }
-      if constexpr (COUNT) np += (!done && has1 && e1.r < 1.0f);
-      {
-        const bool u = !done && has1 && e1.use;
-        const float a = u ? e1.alpha : 0.0f;
-        const float Tn = T * (1.0f - a);
-        const bool term = u && Tn < cfg.tmin;
-        done = done || term;
-        const bool ok = u && !term;
-        const float w = ok ? a * T : 0.0f;
-        const float4 q = s_q[j1];
-        const float2 c2 = s_s[j1];
-        C0 = fmaf(q.w, w, C0);
-        C1 = fmaf(c2.x, w, C1);
-        C2 = fmaf(c2.y, w, C2);
-        T = ok ? Tn : T;
-        last = ok ? rel + j1 + 1 : last;
-      }
+      if (__all_sync(kFull, done0 && done1)) break;
+      blend(list[i]);
+      if (i + 1 < cnt) blend(list[i + 1]);
     }
   }
-  if (inside) {
-    const size_t plane = (size_t)v.W * v.H;
-    const size_t pix = (size_t)y * v.W + x;
-    float* img = image + (size_t)v.pix_off * 3;
-    img[pix] = fmaf(T, cfg.bg[0], C0);
-    img[plane + pix] = fmaf(T, cfg.bg[1], C1);
-    img[2 * plane + pix] = fmaf(T, cfg.bg[2], C2);
-    Tfin[v.pix_off + pix] = T;
-    lastc[v.pix_off + pix] = last;
-    if constexpr (COUNT) pairs[v.pix_off + pix] = np;
+  const size_t plane = (size_t)v.W * v.H;
+  float* img = image + (size_t)v.pix_off * 3;
+  if (in0) {
+    const size_t pix = (size_t)y0 * v.W + x;
+    img[pix] = fmaf(T.x, cfg.bg[0], C0.x);
+    img[plane + pix] = fmaf(T.x, cfg.bg[1], C1.x);
+    img[2 * plane + pix] = fmaf(T.x, cfg.bg[2], C2.x);
+    Tfin[v.pix_off + pix] = T.x;
+    lastc[v.pix_off + pix] = last0;
+    if constexpr (COUNT) pairs[v.pix_off + pix] = np0;
+  }
+  if (in1) {
+    const size_t pix = (size_t)y1 * v.W + x;
+    img[pix] = fmaf(T.y, cfg.bg[0], C0.y);
+    img[plane + pix] = fmaf(T.y, cfg.bg[1], C1.y);
+    img[2 * plane + pix] = fmaf(T.y, cfg.bg[2], C2.y);
+    Tfin[v.pix_off + pix] = T.y;
+    lastc[v.pix_off + pix] = last1;
+    if constexpr (COUNT) pairs[v.pix_off + pix] = np1;
   }
 }
 
@@ -360,7 +407,10 @@ __device__ __forceinline__ int writer_of(int lane) {
 // from its block's last contributor in batches of 32 entries: each lane
 // stages one record, the batch is culled to the entries whose support meets
 // the block, those are processed, and each record the block used is flushed
-// by its lane with one vector atomic add per (record, block).
+// by its lane with one vector atomic add per (record, block).  The pair
+// evaluation and the per-pixel recurrences (T, the colour behind) run in
+// packed pairs over the lane's two pixels; the two share dx, so a lane's
+// sums of q dx, q dx^2 and q dx dy take dx out of the sum.
 template <int TW, int TH>
 __global__ void __launch_bounds__(32)
     render_bwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
@@ -372,8 +422,7 @@ __global__ void __launch_bounds__(32)
   constexpr int WB = 32;             // entries per batch: one per lane
   constexpr int BPT = TW * TH / 64;  // 8x8 blocks per tile
   constexpr int WPR = TW / 8;        // blocks per row of the tile
-  __shared__ float4 s_p[WB], s_q[WB];
-  __shared__ float2 s_s[WB];
+  __shared__ float4 s_A[WB], s_B[WB], s_C[WB], s_D[WB], s_E[WB];
   __shared__ uint32_t s_rec[WB];
   __shared__ float s_acc[10][WB + 1];  // +1: the 10 writer lanes hit 10 different banks
   __shared__ uint8_t s_list[WB];
@@ -390,38 +439,41 @@ __global__ void __launch_bounds__(32)
   const int bx = (wb % WPR) * 8, by = (wb / WPR) * 8;
   const int lx = bx + (lane & 7), ly = by + (lane >> 3);
   const int x = tx * TW + lx;
-  const float fx = (float)lx + 0.5f;
-  float fy[2], T[2], G0[2], G1[2], G2[2], B0[2], B1[2], B2[2];
-  uint32_t last[2];
-  uint32_t mylast = 0;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int y = ty * TH + ly + 4 * k;
-    fy[k] = (float)(ly + 4 * k) + 0.5f;
-    T[k] = 1.0f;
-    G0[k] = G1[k] = G2[k] = 0.0f;
-    last[k] = 0;
-    if (x < v.W && y < v.H) {
-      const size_t plane = (size_t)v.W * v.H;
-      const size_t pix = (size_t)y * v.W + x;
-      const float* gi = dLdimg + (size_t)v.pix_off * 3;
-      G0[k] = gi[pix];
-      G1[k] = gi[plane + pix];
-      G2[k] = gi[2 * plane + pix];
-      T[k] = Tfin[v.pix_off + pix];
-      last[k] = lastc[v.pix_off + pix];
+  // per-pixel state of the lane's two pixels, packed: .x row ly, .y row ly + 4
+  const float2 fx = make_float2((float)lx + 0.5f, (float)lx + 0.5f);
+  const float2 fy = make_float2((float)ly + 0.5f, (float)(ly + 4) + 0.5f);
+  float2 T = make_float2(1.0f, 1.0f), G0 = make_float2(0.0f, 0.0f), G1 = G0, G2 = G0;
+  // colour behind the current record, normalised by the transmittance after it
+  float2 B0 = make_float2(cfg.bg[0], cfg.bg[0]), B1 = make_float2(cfg.bg[1], cfg.bg[1]),
+         B2 = make_float2(cfg.bg[2], cfg.bg[2]);
+  uint32_t last0 = 0, last1 = 0;
+  {
+    const size_t plane = (size_t)v.W * v.H;
+    const float* gi = dLdimg + (size_t)v.pix_off * 3;
+    const int y0 = ty * TH + ly, y1 = y0 + 4;
+    if (x < v.W && y0 < v.H) {
+      const size_t pix = (size_t)y0 * v.W + x;
+      G0.x = gi[pix];
+      G1.x = gi[plane + pix];
+      G2.x = gi[2 * plane + pix];
+      T.x = Tfin[v.pix_off + pix];
+      last0 = lastc[v.pix_off + pix];
     }
-    // colour behind the current record, normalised by the transmittance after it
-    B0[k] = cfg.bg[0];
-    B1[k] = cfg.bg[1];
-    B2[k] = cfg.bg[2];
-    mylast = max(mylast, last[k]);
+    if (x < v.W && y1 < v.H) {
+      const size_t pix = (size_t)y1 * v.W + x;
+      G0.y = gi[pix];
+      G1.y = gi[plane + pix];
+      G2.y = gi[2 * plane + pix];
+      T.y = Tfin[v.pix_off + pix];
+      last1 = lastc[v.pix_off + pix];
+    }
   }
-  const uint32_t wlast = __reduce_max_sync(kFull, mylast);
+  const uint32_t wlast = __reduce_max_sync(kFull, max(last0, last1));
   if (wlast == 0) return;
   const float ox = (float)(tx * TW), oy = (float)(ty * TH);
   const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 7.0f;
   const float lg2_amin = lg2_approx(cfg.amin);
+  const float2 one = make_float2(1.0f, 1.0f), neg1 = make_float2(-1.0f, -1.0f);
   const int wslot = writer_of(lane);
   for (int hi = (int)wlast; hi > 0; hi -= WB) {
     const int lo = hi - WB > 0 ? hi - WB : 0;
@@ -434,9 +486,12 @@ __global__ void __launch_bounds__(32)
       float rc;
       stage_record(rec4, r, ox, oy, lg2_amin, st, box, rc);
       s_rec[lane] = r;
-      s_p[lane] = st.p;
-      s_q[lane] = st.q;
-      s_s[lane] = st.s;
+      const Staged2 s2 = pack_staged(st);
+      s_A[lane] = s2.A;
+      s_B[lane] = s2.Bc;
+      s_C[lane] = s2.Cc;
+      s_D[lane] = s2.D;
+      s_E[lane] = s2.E;
       listed = box_hits(box, wx0, wx1, wy0, wy1) && ellipse_hits(st.p, st.q.x, rc, wx0, wx1, wy0, wy1);
     }
     const unsigned lm = __ballot_sync(kFull, listed);
@@ -445,49 +500,51 @@ __global__ void __launch_bounds__(32)
     unsigned touched = 0;  // entries the block used (warp-uniform)
     for (int i = __popc(lm) - 1; i >= 0; --i) {
       const int j = s_list[i];
-      const float4 p = s_p[j], q = s_q[j];
-      const float2 c2 = s_s[j];
-      PairEval e[2];
-      bool use[2], any = false;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        eval_pair<true>(fx, fy[k], p, q, cfg.amin, cfg.amax, e[k]);
-        use[k] = e[k].use && (uint32_t)(lo + j) < last[k];  // pairs the forward composited
-        any = any || use[k];
-      }
-      const unsigned hits = __ballot_sync(kFull, any);
+      const float4 D = s_D[j], E = s_E[j];
+      PairEval2 e;
+      eval_pair2<true>(fx, fy, s_A[j], s_B[j], s_C[j], D, cfg.amax, e);
+      // pairs the forward composited
+      const bool use0 = e.r.x < 1.0f && e.alpha.x >= cfg.amin && (uint32_t)(lo + j) < last0;
+      const bool use1 = e.r.y < 1.0f && e.alpha.y >= cfg.amin && (uint32_t)(lo + j) < last1;
+      const unsigned hits = __ballot_sync(kFull, use0 || use1);
       if (hits == 0) continue;  // no pixel of the block: T and B stay
       touched |= 1u << j;
+      // branch-free: a pair the forward skipped contributes zero and leaves T, B
+      const float2 a = make_float2(use0 ? e.alpha.x : 0.0f, use1 ? e.alpha.y : 0.0f);
+      const float2 oma = fma2(a, neg1, one);
+      T = mul2(T, make_float2(rcp_approx(oma.x), rcp_approx(oma.y)));  // transmittance before this record
+      const float2 w = mul2(a, T);
       float gv[10];
-#pragma unroll
-      for (int m = 0; m < 10; ++m) gv[m] = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        // branch-free: a pair the forward skipped contributes zero and leaves T, B
-        const float a = use[k] ? e[k].alpha : 0.0f;
-        T[k] = __fdividef(T[k], 1.0f - a);  // transmittance before this record
-        const float w = a * T[k];
-        gv[7] = fmaf(w, G0[k], gv[7]);
-        gv[8] = fmaf(w, G1[k], gv[8]);
-        gv[9] = fmaf(w, G2[k], gv[9]);
-        const float d0 = q.w - B0[k], d1 = c2.x - B1[k], d2 = c2.y - B2[k];
-        const float dalpha = T[k] * fmaf(d0, G0[k], fmaf(d1, G1[k], d2 * G2[k]));
-        B0[k] = fmaf(a, d0, B0[k]);
-        B1[k] = fmaf(a, d1, B1[k]);
-        B2[k] = fmaf(a, d2, B2[k]);
-        const float ga = a < cfg.amax ? dalpha * a : 0.0f;
-        const float qq = __fdividef(ga, e[k].om);  // ga = 0 unless composited; 1 - r > 0
-        const float u0 = qq * e[k].dx, u1 = qq * e[k].dy;
-        gv[0] += u0;
-        gv[1] += u1;
-        gv[2] = fmaf(u0, e[k].dx, gv[2]);
-        gv[3] = fmaf(u0, e[k].dy, gv[3]);
-        gv[4] = fmaf(u1, e[k].dy, gv[4]);
-        gv[5] += ga;
-        gv[6] = fmaf(ga, e[k].lg, gv[6]);
+      {
+        const float2 c0 = hi2(D), c1 = lo2(E), c2 = hi2(E);
+        const float2 e0 = fma2(B0, neg1, c0), e1 = fma2(B1, neg1, c1), e2 = fma2(B2, neg1, c2);
+        const float2 dal = mul2(T, fma2(e0, G0, fma2(e1, G1, mul2(e2, G2))));
+        B0 = fma2(a, e0, B0);
+        B1 = fma2(a, e1, B1);
+        B2 = fma2(a, e2, B2);
+        const float2 wg0 = mul2(w, G0), wg1 = mul2(w, G1), wg2 = mul2(w, G2);
+        gv[7] = wg0.x + wg0.y;
+        gv[8] = wg1.x + wg1.y;
+        gv[9] = wg2.x + wg2.y;
+        float2 ga = mul2(dal, a);
+        ga.x = a.x < cfg.amax ? ga.x : 0.0f;
+        ga.y = a.y < cfg.amax ? ga.y : 0.0f;
+        // q = ga / (1 - r): ga = 0 unless composited, and 1 - r > 0
+        const float2 qq = mul2(ga, make_float2(rcp_approx(e.om.x), rcp_approx(e.om.y)));
+        const float2 u1 = mul2(qq, e.dy);
+        const float2 u1y = mul2(u1, e.dy);
+        const float2 glg = mul2(ga, e.lg);
+        // dx is the same for both pixels: sums of q dx and q dx dy factor it
+        gv[0] = (qq.x + qq.y) * e.dx.x;
+        gv[1] = u1.x + u1.y;
+        gv[2] = gv[0] * e.dx.x;
+        gv[3] = gv[1] * e.dx.x;
+        gv[4] = u1y.x + u1y.y;
+        gv[5] = ga.x + ga.y;
+        gv[6] = glg.x + glg.y;
       }
       if (__popc(hits) == 1) {  // one lane: its values are the totals
-        if (any) {
+        if (use0 || use1) {
 #pragma unroll
           for (int m = 0; m < 10; ++m) s_acc[m][j] = gv[m];
         }
@@ -498,8 +555,7 @@ __global__ void __launch_bounds__(32)
     }
     __syncwarp();
     if ((touched >> lane) & 1u) {
-      const float4 p = s_p[lane], q = s_q[lane];
-      const float a = p.z, b = 0.5f * p.w, c = q.x, beta = q.z;
+      const float a = s_B[lane].x, b = 0.5f * s_B[lane].z, c = s_C[lane].x, beta = s_C[lane].z;
       const float v0 = s_acc[0][lane], v1 = s_acc[1][lane];
       float4* dst = g2d + 3 * (size_t)s_rec[lane];
       atomicAdd(dst, make_float4(2.0f * beta * (a * v0 + b * v1), 2.0f * beta * (b * v0 + c * v1),
@@ -536,14 +592,14 @@ cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cu
   const Header* hdr = (const Header*)(ws + L.header);
   const uint32_t R = L.R > 0 ? L.R : 1;
   constexpr int NT = TW * TH;
+  const uint32_t* order = order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr;
   if (cfg.flags & 2)  // diagnostic variant: also count visited pairs with r < 1 per pixel
-    launch_dependent(render_fwd_kernel<TW, TH, true>, dim3(L.NT), dim3(NT), 0, st, views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
-                                                       image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs),
-                                                       order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr, L.NT, L.cap);
+    launch_dependent(render_fwd_kernel<TW, TH, true>, dim3(L.NT), dim3(NT / 2), 0, st, views, L.V, cfg, tstart,
+                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs), order,
+                     L.NT, L.cap);
   else
-    launch_dependent(render_fwd_kernel<TW, TH, false>, dim3(L.NT), dim3(NT), 0, st, views, L.V, cfg, tstart, sorted_instances(L, ws), rec4,
-                                                        image, Tfin, last, hdr, R, nullptr,
-                                                        order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr, L.NT, L.cap);
+    launch_dependent(render_fwd_kernel<TW, TH, false>, dim3(L.NT), dim3(NT / 2), 0, st, views, L.V, cfg, tstart,
+                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, nullptr, order, L.NT, L.cap);
   return cudaGetLastError();
 }
 
