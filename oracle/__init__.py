@@ -23,6 +23,11 @@ Modules
                conditioning and opacity (Sec. 4.3), EWA projection and the
                Beta kernel (Sec. 3), front-to-back compositing (Sec. 3);
                gradients by autograd of that float64 forward.
+``train64``    the training step around the rasterizer (Sec. 4.5 loss,
+               Sec. 5.1 optimiser): L1 + (1 - SSIM) image loss with its
+               float64 autograd gradient, and the Adam step on raw
+               parameters with the activation chain, the opacity and scale
+               penalties and the spatial noise.
 
 Every function names the passage it follows.  Parity status of each function
 is given in its module header.
