@@ -38,6 +38,13 @@ L2_BYTES = 129 * 2 ** 20
 # MUFU operations are bounded separately, see the design notes)
 FWD_FP32_PER_PAIR, FWD_MUFU_PER_PAIR = 16, 2
 BWD_FP32_PER_PAIR, BWD_MUFU_PER_PAIR = 45, 3
+# training step: the image loss reads the image and the target and writes
+# dL/dimage (12 B per pixel and channel); its work is the two separable 11-tap
+# passes of the five SSIM window statistics (110 FMA) and of the three partial
+# derivatives (66 FMA) plus ~30 operations of the map and its derivatives.
+# Adam reads raw, grad, m, v and writes raw, m, v and the activated value.
+LOSS_BYTES_PER_PC, LOSS_FP32_PER_PC = 12, 206
+ADAM_BYTES_PER_PARAM = 32
 
 
 def parse():
@@ -382,6 +389,7 @@ def bench_ours(args, rank, world, local):
     del graph
     # end to end through the public API with host buffers
     e2e = bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view)
+    train = bench_train(r, ds, wl, args, dev, pk, n_sm, flush) if rank == 0 and world == 1 else None
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "MP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -399,6 +407,7 @@ def bench_ours(args, rank, world, local):
         "roofline_path": path_roof,
         "graph": graph_out,
         "e2e": e2e,
+        "train_step": train,
         "gpu_launches": kernels_per_step(r) * args.steps,
         "clocks": clk,
         "wall_s_timed_loop": round(wall, 3),
@@ -409,6 +418,79 @@ def bench_ours(args, rank, world, local):
     if dist:
         dist.destroy_process_group()
     return out
+
+
+def bench_train(r, ds, wl, args, dev, pk, n_sm, flush):
+    """One training iteration of Sec. 4.5/5.1 on the same view: render,
+    image loss (L1 + 0.2 (1 - SSIM)) and its gradient, backward, Adam with
+    the paper's learning rates and penalties, spatial noise drawn outside the
+    timed region.  Per-stage CUDA events; L2 flushed between steps.  The
+    scene's parameters change every step (the optimiser updates them)."""
+    import torch
+
+    from paper_2510_03312_gb300 import scenes as S
+    from paper_2510_03312_gb300 import train as TR
+
+    target = r.pack(S.l1_target(1, wl.views))
+    loss_fn = TR.ImageLoss(wl.views, device=dev)
+    params0 = ds.params.clone()
+    opt = TR.Adam(wl.scenes[0], ds.params)
+    noise = torch.randn(3, ds.P, device=dev) * 1e-4
+    dL = torch.empty_like(target)
+    stream = torch.cuda.current_stream()
+    names = ["preprocess", "bin_sort", "render_fwd", "image_loss", "render_bwd_blend", "render_bwd_params", "adam"]
+    img_holder = {}
+
+    def step(evs):
+        calls = [r.preprocess, r.bin_sort, lambda: img_holder.update(img=r.render_fwd()),
+                 lambda: loss_fn(img_holder["img"], target, dL), lambda: r.render_bwd_blend(dL),
+                 lambda: img_holder.update(g=r.render_bwd_params()), lambda: opt.step(img_holder["g"][0], noise)]
+        evs[0].record(stream)
+        for k, c in enumerate(calls):
+            c()
+            evs[k + 1].record(stream)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    rows = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_((i + 11) & 0xFF)
+        evs = [ev() for _ in range(len(names) + 1)]
+        step(evs)
+        if i >= args.warmup:
+            rows.append(evs)
+    torch.cuda.synchronize()
+    loss_last = float(loss_fn.loss[0])
+    stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(len(names))] for e in rows]).mean(0)
+    with torch.no_grad():
+        ds.params.copy_(params0)  # leave the scene as the other measurements found it
+    step_ms = float(stage.sum())
+    v = wl.views[0]
+    pc = 3 * v.width * v.height
+    n_par = ds.params.numel()
+    alu_peak = alu_peak_tops(n_sm, pk.get("sm_max_mhz", 2070.0))
+    t_loss = stage[names.index("image_loss")] * 1e-3
+    t_adam = stage[names.index("adam")] * 1e-3
+    loss_ops = LOSS_FP32_PER_PC * pc
+    loss_bytes = LOSS_BYTES_PER_PC * pc
+    adam_bytes = ADAM_BYTES_PER_PARAM * n_par
+    return {
+        "ms_per_step": round(step_ms, 4),
+        "MP_per_s": round(v.width * v.height / 1e6 / (step_ms * 1e-3), 2),
+        "stage_ms": {n: round(float(m), 4) for n, m in zip(names, stage)},
+        "loss_after_steps": round(loss_last, 6),
+        "roofline": {
+            "image_loss": {"bound": "alu", "fp32_ops": loss_ops, "bytes": loss_bytes,
+                           "achieved": round(loss_ops / t_loss / 1e12, 3), "peak": round(alu_peak, 2),
+                           "unit": "TFLOP/s", "frac": round(loss_ops / t_loss / 1e12 / alu_peak, 4),
+                           "hbm_frac": round(loss_bytes / t_loss / 1e9 / pk["hbm_gbs"], 4)},
+            "adam": {"bound": "hbm", "bytes": adam_bytes, "achieved": round(adam_bytes / t_adam / 1e9, 1),
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(adam_bytes / t_adam / 1e9 / pk["hbm_gbs"], 4)},
+        },
+        "work": f"{pc} pixel-channels ({LOSS_FP32_PER_PC} FP32 ops, {LOSS_BYTES_PER_PC} B each); "
+                f"{n_par} parameters x {ADAM_BYTES_PER_PARAM} B",
+    }
 
 
 def bench_e2e(r, ds, dL, args, dev, world, dist, mp_per_view):

@@ -16,6 +16,10 @@
  *   ubs_render_bwd  gradients of the rendered images with respect to every
  *                   primitive parameter (differentiable rendering, Sec. 4.5)
  *
+ * and the training step around it: ubs_image_loss (the image loss of
+ * Sec. 4.5 and its gradient) and ubs_adam_step (the optimiser of Sec. 5.1
+ * with the penalties and noise of Sec. 4.5).
+ *
  * Conventions shared by every call
  * --------------------------------
  * Memory: every pointer in ubs_scene, ubs_scene_grad, the image and dL/dimage
@@ -233,6 +237,68 @@ ubs_status ubs_export(const ubs_problem* problem, void* workspace, size_t worksp
                       cudaStream_t stream);
 
 const char* ubs_status_string(ubs_status status);
+
+/* ---------------------------------------------------------------------------
+ * The training step around the rasterizer (Sec. 4.5 loss, Sec. 5.1 optimiser)
+ * ------------------------------------------------------------------------- */
+
+/* Image loss of Sec. 4.5, (1 - lambda_ssim) L1 + lambda_ssim (1 - SSIM), and
+ * its gradient.  Readings: L1 is the mean |C - C*| over a view's pixels and
+ * channels; SSIM is the mean structural-similarity map of Wang et al. (2004)
+ * per channel, with an 11 x 11 Gaussian window of standard deviation 1.5,
+ * C1 = 0.01^2, C2 = 0.03^2 and zero padding at the border (a map of the
+ * image's size); over several views the loss is the mean of the views'.
+ * Images and targets are packed like the rasterizer's (view v planar
+ * [3][heights[v]][widths[v]], views back to back).  widths/heights are host
+ * arrays [n_views], 1 <= n_views <= 256.
+ *
+ * ubs_loss_workspace_size: bytes of workspace (0 on invalid arguments).
+ * ubs_image_loss: writes dL/dimage (device, packed like the images; it may
+ *   not alias image or target) and loss (device float[1 + n_views]: the
+ *   total, then each view's loss).  workspace: device, 256-byte aligned, at
+ *   least ubs_loss_workspace_size bytes, holding the per-pixel partial
+ *   derivatives of SSIM and per-block sums between the kernels.  The sums are
+ *   reduced in a fixed order: results are deterministic.  Asynchronous on
+ *   `stream`; allocates nothing. */
+size_t ubs_loss_workspace_size(int32_t n_views, const int32_t* widths, const int32_t* heights);
+ubs_status ubs_image_loss(int32_t n_views, const int32_t* widths, const int32_t* heights, const float* image,
+                          const float* target, float lambda_ssim, float* dL_dimage, float* loss,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+enum { UBS_ACT_IDENTITY = 0, UBS_ACT_SIGMOID = 1, UBS_ACT_EXP = 2 };
+
+/* One parameter plane of the optimiser step. */
+typedef struct {
+  float lr;           /* Adam learning rate of the plane (Sec. 5.1: 1.6e-4 positions,
+                         5e-2 opacity, 5e-3 scales, 1e-3 the rest) */
+  int32_t activation; /* UBS_ACT_*: the renderer reads act(raw) */
+  float l1_weight;    /* weight of an L1 penalty on the activated value
+                         (Sec. 4.5: lambda_o on opacity, lambda_Sigma on scales) */
+  int32_t noise_row;  /* row of `noise` added after the update, or -1 */
+} ubs_adam_plane;
+
+typedef struct {
+  float beta1, beta2, eps; /* Adam constants (0.9, 0.999, 1e-15) */
+  int32_t step;            /* t >= 1, for the bias corrections 1 - beta^t */
+  float lambda_eps;        /* weight of the injected noise (Sec. 4.5: 1) */
+} ubs_adam_config;
+
+/* One Adam step (Kingma and Ba 2015) over K planes of P parameters, fused
+ * with the activation and the penalties of Sec. 4.5:
+ *   a = act(raw);  g = grad + l1_weight sign(a);  g_raw = g act'(raw)
+ *   m = beta1 m + (1 - beta1) g_raw;  v = beta2 v + (1 - beta2) g_raw^2
+ *   raw -= lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)
+ *   raw += lambda_eps noise[noise_row]     (the spatial noise of Sec. 4.5)
+ *   act_out = act(raw)
+ * raw, act_out, grad, m, v: device [K][P] planes (plane k at k * P), 4-byte
+ * aligned; grad is dL/d(activated value), as ubs_render_bwd writes it.
+ * act_out is the buffer the rasterizer reads (it may not alias raw).
+ * planes: host array [K], 1 <= K <= 64.  noise: device [rows][P], or NULL
+ * when no plane has noise_row >= 0.  Asynchronous on `stream`; allocates
+ * nothing. */
+ubs_status ubs_adam_step(int32_t K, int64_t P, const ubs_adam_plane* planes, const ubs_adam_config* cfg,
+                         float* raw, float* act_out, const float* grad, float* m, float* v, const float* noise,
+                         cudaStream_t stream);
 
 /* Forward rendering that allocates nothing.  (The paper has no counterpart:
  * this serves callers that cannot allocate device memory when they render,

@@ -29,6 +29,7 @@ UNITS = {
     "prim_backward.cu": [],
     "abi.cu": [],
     "noalloc.cu": [],
+    "train.cu": [],
 }
 
 

@@ -26,6 +26,9 @@ UBS_ROT_SKEW1 = 1
 UBS_FLAG_TIGHT_CUT = 1
 UBS_FLAG_COUNT_PAIRS = 2
 UBS_FLAG_ACCUMULATE_GRADS = 4
+UBS_ACT_IDENTITY = 0
+UBS_ACT_SIGMOID = 1
+UBS_ACT_EXP = 2
 
 EXPORT_KEYS, EXPORT_TILES, EXPORT_RECT, EXPORT_RECORDS, EXPORT_INSTANCES = 0, 1, 2, 3, 4
 EXPORT_TILE_START, EXPORT_FINAL_T, EXPORT_LAST, EXPORT_SCREEN_GRAD, EXPORT_PAIRS = 5, 6, 7, 8, 9
@@ -66,6 +69,15 @@ class ubs_device_status(Structure):
                 ("instances", c_int64)]
 
 
+class ubs_adam_plane(Structure):
+    _fields_ = [("lr", c_float), ("activation", c_int32), ("l1_weight", c_float), ("noise_row", c_int32)]
+
+
+class ubs_adam_config(Structure):
+    _fields_ = [("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("step", c_int32),
+                ("lambda_eps", c_float)]
+
+
 # name -> (restype, argtypes), exactly the declarations of include/ubs.h
 SIGNATURES = {
     "ubs_workspace_size": (c_size_t, [POINTER(ubs_problem)]),
@@ -83,6 +95,11 @@ SIGNATURES = {
                              POINTER(c_size_t), c_void_p]),
     "ubs_status_string": (c_char_p, [c_int32]),
     "ubs_render_fwd_static": (c_int32, [POINTER(ubs_problem), c_void_p, c_void_p]),
+    "ubs_loss_workspace_size": (c_size_t, [c_int32, POINTER(c_int32), POINTER(c_int32)]),
+    "ubs_image_loss": (c_int32, [c_int32, POINTER(c_int32), POINTER(c_int32), c_void_p, c_void_p, c_float,
+                                 c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "ubs_adam_step": (c_int32, [c_int32, c_int64, POINTER(ubs_adam_plane), POINTER(ubs_adam_config), c_void_p,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -159,3 +176,25 @@ def ubs_status_string(status) -> str:
 
 def ubs_render_fwd_static(problem, image, stream) -> int:
     return int(load().ubs_render_fwd_static(ctypes.byref(problem), image, stream))
+
+
+def _sizes(widths, heights):
+    n = len(widths)
+    return n, (c_int32 * n)(*[int(w) for w in widths]), (c_int32 * n)(*[int(h) for h in heights])
+
+
+def ubs_loss_workspace_size(widths, heights) -> int:
+    n, w, h = _sizes(widths, heights)
+    return int(load().ubs_loss_workspace_size(n, w, h))
+
+
+def ubs_image_loss(widths, heights, image, target, lambda_ssim, dL_dimage, loss, workspace, workspace_bytes,
+                   stream) -> int:
+    n, w, h = _sizes(widths, heights)
+    return int(load().ubs_image_loss(n, w, h, image, target, float(lambda_ssim), dL_dimage, loss, workspace,
+                                     workspace_bytes, stream))
+
+
+def ubs_adam_step(K, P, planes, cfg, raw, act_out, grad, m, v, noise, stream) -> int:
+    return int(load().ubs_adam_step(int(K), int(P), planes, ctypes.byref(cfg), raw, act_out, grad, m, v, noise,
+                                    stream))

@@ -104,3 +104,63 @@ def test_workspace_checks(lib):
     assert U.ubs_bin_sort(pr, 0x100000, need - 256, None) == U.UBS_ERR_WORKSPACE
     keep[0][0].mean_x = 0x10002
     assert U.ubs_preprocess(pr, 0x100000, need, None) == U.UBS_ERR_ALIGNMENT
+
+
+def test_loss_workspace_size_arithmetic(lib):
+    # three partial planes per pixel and channel, then one float2 per 32x32 block of each channel
+    w, h = [1600, 33], [1060, 17]
+    pix = sum(a * b for a, b in zip(w, h))
+    blocks = sum(3 * ((a + 31) // 32) * ((b + 31) // 32) for a, b in zip(w, h))
+    want = ((9 * pix * 4 + 255) // 256) * 256 + ((blocks * 8 + 255) // 256) * 256
+    assert U.ubs_loss_workspace_size(w, h) == want
+    assert U.ubs_loss_workspace_size([], []) == 0
+    assert U.ubs_loss_workspace_size([0], [10]) == 0
+    assert U.ubs_loss_workspace_size([10] * 257, [10] * 257) == 0
+
+
+def test_image_loss_rejects_bad_arguments_before_launching(lib):
+    fake = 0x10000
+    ws = U.ubs_loss_workspace_size([64], [48])
+    ok = dict(widths=[64], heights=[48], image=fake, target=fake, lambda_ssim=0.2, dL_dimage=fake, loss=fake,
+              workspace=fake, workspace_bytes=ws, stream=None)
+
+    def call(**kw):
+        a = dict(ok)
+        a.update(kw)
+        return U.ubs_image_loss(**a)
+
+    assert call(image=None) == U.UBS_ERR_INVALID_ARG
+    assert call(loss=None) == U.UBS_ERR_INVALID_ARG
+    assert call(lambda_ssim=1.5) == U.UBS_ERR_INVALID_ARG
+    assert call(widths=[0]) == U.UBS_ERR_INVALID_ARG
+    assert call(workspace=fake + 16) == U.UBS_ERR_ALIGNMENT
+    assert call(image=fake + 2) == U.UBS_ERR_ALIGNMENT
+    assert call(workspace_bytes=ws - 1) == U.UBS_ERR_WORKSPACE
+
+
+def test_adam_step_rejects_bad_arguments_before_launching(lib):
+    fake = 0x10000
+    K, P = 3, 40
+    planes = (U.ubs_adam_plane * K)()
+    for k in range(K):
+        planes[k].lr, planes[k].activation, planes[k].noise_row = 1e-3, U.UBS_ACT_IDENTITY, -1
+    cfg = U.ubs_adam_config(0.9, 0.999, 1e-15, 1, 1.0)
+    bufs = [fake, fake + 0x1000, fake + 0x2000, fake + 0x3000, fake + 0x4000]
+
+    def call(K=K, P=P, planes=planes, cfg=cfg, bufs=bufs, noise=None):
+        return U.ubs_adam_step(K, P, planes, cfg, *bufs, noise, None)
+
+    assert call(K=0) == U.UBS_ERR_INVALID_ARG
+    assert call(K=65) == U.UBS_ERR_INVALID_ARG
+    assert call(P=-1) == U.UBS_ERR_INVALID_ARG
+    assert call(P=0) == U.UBS_OK  # nothing to do, nothing launched
+    assert call(bufs=[fake, fake] + bufs[2:]) == U.UBS_ERR_INVALID_ARG  # act_out aliases raw
+    assert call(bufs=[None] + bufs[1:]) == U.UBS_ERR_INVALID_ARG
+    assert call(bufs=[fake + 2] + bufs[1:]) == U.UBS_ERR_ALIGNMENT
+    bad = U.ubs_adam_config(0.9, 0.999, 1e-15, 0, 1.0)
+    assert call(cfg=bad) == U.UBS_ERR_INVALID_ARG
+    planes[1].activation = 7
+    assert call() == U.UBS_ERR_INVALID_ARG
+    planes[1].activation = U.UBS_ACT_SIGMOID
+    planes[0].noise_row = 0
+    assert call(noise=None) == U.UBS_ERR_INVALID_ARG
