@@ -102,9 +102,16 @@ def _planes(scene):
 
 def rotation(scene):
     """R_x rows as a 3x3 nested list of [P] arrays.  Quaternion mode: the
-    3DGS rotation of the normalised quaternion (Sec. 3); skew mode: R = I + A
-    (first-order Taylor of exp(A), Sec. 4.2 and the appendix on the
-    spatial-orthogonal Cholesky parameterisation)."""
+    3DGS rotation of the normalised quaternion (Sec. 3).  Skew modes, from
+    omega (appendix on the spatial-orthogonal Cholesky parameterisation):
+    R = I + A (first-order Taylor), and with the squares and products
+    a_ij = o_i o_j
+        R = I + l A + k A^2,  (A^2)_ij = a_ij - delta_ij (a11 + a22 + a33),
+    k = 1/2, l = 1 (second-order Taylor) or k = l = 2 / (1 + ((a11 + a22) + a33))
+    (Cayley: (I - A)^{-1}(I + A) in closed form), evaluated entry by entry as
+        R00 = 1 - k (a22 + a33)   R01 = k a12 - l o3   R02 = k a13 + l o2
+        R10 = k a12 + l o3        R11 = 1 - k (a11 + a33)   R12 = k a23 - l o1
+        R20 = k a13 - l o2        R21 = k a23 + l o1   R22 = 1 - k (a11 + a22)."""
     pl = _planes(scene)
     rot = pl["rot"]
     if scene.rot_mode == 0:
@@ -116,10 +123,26 @@ def rotation(scene):
         R = [[one - two * (y * y + z * z), two * (x * y - w * z), two * (x * z + w * y)],
              [two * (x * y + w * z), one - two * (x * x + z * z), two * (y * z - w * x)],
              [two * (x * z - w * y), two * (y * z + w * x), one - two * (x * x + y * y)]]
-    else:
+    elif scene.rot_mode == 1:
         o1, o2, o3 = rot[0], rot[1], rot[2]
         one = np.ones_like(o1)
         R = [[one, -o3, o2], [o3, one, -o1], [-o2, o1, one]]
+    elif scene.rot_mode in (2, 3):
+        o1, o2, o3 = rot[0], rot[1], rot[2]
+        a11, a22, a33 = o1 * o1, o2 * o2, o3 * o3
+        a12, a13, a23 = o1 * o2, o1 * o3, o2 * o3
+        one = F(1)
+        if scene.rot_mode == 2:
+            k = np.full_like(o1, F(0.5))
+            l = np.ones_like(o1)
+        else:
+            k = F(2) / (one + ((a11 + a22) + a33))
+            l = k
+        R = [[one - k * (a22 + a33), k * a12 - l * o3, k * a13 + l * o2],
+             [k * a12 + l * o3, one - k * (a11 + a33), k * a23 - l * o1],
+             [k * a13 - l * o2, k * a23 + l * o1, one - k * (a11 + a22)]]
+    else:
+        raise ValueError(f"rotation mode {scene.rot_mode}")
     return R
 
 

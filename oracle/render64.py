@@ -4,8 +4,10 @@ Plain PyTorch CPU float64 operations, written to be read against the paper:
 
 * Sec. 4.2, spatial-orthogonal Cholesky parameterisation:
   L = [[R_x diag(s_x), 0], [L_qx, L_q]], Sigma = L L^T, with R_x the 3DGS
-  quaternion rotation (Sec. 3) or R_x = I + A(omega) (appendix on the
-  spatial-orthogonal Cholesky parameterisation, first-order Taylor).
+  quaternion rotation (Sec. 3) or R_x from the skew matrix A(omega) (appendix
+  on the spatial-orthogonal Cholesky parameterisation): I + A (first-order
+  Taylor, the paper's choice), I + A + A^2/2 (second order) or the Cayley
+  transform (I - A)^{-1}(I + A).
 * Sec. 4.3, Beta-modulated conditional slicing:
   beta_x = 4 exp(b_x), beta_q = exp(b_q), beta~ = [beta_q]_{<=1};
   mu_{x|q} = mu_x + Sigma_xq Sigma_q^{-1} diag(beta~) (q - mu_q);
@@ -32,7 +34,9 @@ pixel is flagged and every admissible branch is enumerated.
 
 Gradients are the autograd gradients of this float64 forward.
 
-Parity: pinned (tests/test_oracle_*.py): closed-form footprints, brute-force
+Parity: pinned (tests/test_oracle_*.py): the quaternion, Cayley and
+second-order rotations against SciPy (rotation map, rotation vector, expm),
+closed-form footprints, brute-force
 depth-sorted compositing, transmittance invariants, the static reduction of
 N=6/7 to N=3, Gaussian conditioning at beta~ = 1 against the precision-block
 identity, the Gaussian limit of the Beta kernel, the paper's printed beta
@@ -60,9 +64,22 @@ def scene_leaves(scene, requires_grad=False):
     return out
 
 
+def skew64(rot):
+    """[P, 3, 3] skew matrix A(omega) = [[0,-w3,w2],[w3,0,-w1],[-w2,w1,0]]."""
+    w1, w2, w3 = rot[0], rot[1], rot[2]
+    zero = torch.zeros_like(w1)
+    rows = [torch.stack([zero, -w3, w2], -1), torch.stack([w3, zero, -w1], -1),
+            torch.stack([-w2, w1, zero], -1)]
+    return torch.stack(rows, -2)
+
+
 def rotation64(rot, rot_mode):
-    """[P, 3, 3] rotation.  Quaternion (w, x, y, z) normalised, 3DGS formula;
-    skew mode R = I + A(omega) with A = [[0,-w3,w2],[w3,0,-w1],[-w2,w1,0]]."""
+    """[P, 3, 3] rotation R_x.  Quaternion (w, x, y, z) normalised, 3DGS
+    formula (Sec. 3); the skew-symmetric forms of the appendix on the
+    spatial-orthogonal Cholesky parameterisation (its table of rotation
+    parameterisations): R = I + A (first-order Taylor of exp A, the paper's
+    choice), R = I + A + A^2/2 (second-order Taylor) and the Cayley transform
+    R = (I - A)^{-1} (I + A), each written as its definition."""
     if rot_mode == 0:
         q = rot / torch.sqrt((rot * rot).sum(0, keepdim=True))
         w, x, y, z = q[0], q[1], q[2], q[3]
@@ -71,12 +88,16 @@ def rotation64(rot, rot_mode):
             torch.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
             torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1),
         ]
-    else:
-        w1, w2, w3 = rot[0], rot[1], rot[2]
-        one, zero = torch.ones_like(w1), torch.zeros_like(w1)
-        rows = [torch.stack([one, -w3, w2], -1), torch.stack([w3, one, -w1], -1),
-                torch.stack([-w2, w1, one], -1)]
-    return torch.stack(rows, -2)
+        return torch.stack(rows, -2)
+    A = skew64(rot)
+    eye = torch.eye(3, dtype=A.dtype).expand_as(A)
+    if rot_mode == 1:
+        return eye + A
+    if rot_mode == 2:
+        return eye + A + 0.5 * (A @ A)
+    if rot_mode == 3:
+        return torch.linalg.solve(eye - A, eye + A)
+    raise ValueError(f"rotation mode {rot_mode}")
 
 
 def build_L(leaves, N, rot_mode):

@@ -15,6 +15,7 @@ Layout (all float32, structure of arrays, one plane per scalar, stride P):
                                         [d] (N=6), [t] (N=4)
     rot           4 (quat) / 3 (skew)   quaternion (w, x, y, z), not normalised,
                                         or omega of the skew matrix A(omega)
+                                        (first- or second-order Taylor, Cayley)
     scale_x       3                     spatial scales s_x > 0
     L_qx          3C                    C x 3 block, row-major (k, j) -> 3k + j
     L_q           C(C+1)/2              lower-triangular block, packed row-major
@@ -34,7 +35,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 ROT_QUAT = 0
-ROT_SKEW1 = 1
+ROT_SKEW1 = 1   # R = I + A(omega), the paper's first-order Taylor
+ROT_SKEW2 = 2   # R = I + A + A^2 / 2, second-order Taylor
+ROT_CAYLEY = 3  # R = (I - A)^-1 (I + A), the Cayley transform
+ROT_MODES = (ROT_QUAT, ROT_SKEW1, ROT_SKEW2, ROT_CAYLEY)
 
 PLANE_ORDER = ("mean_x", "mean_q", "rot", "scale_x", "L_qx", "L_q", "b", "opacity", "rgb")
 

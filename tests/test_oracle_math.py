@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import fp32_spec
 from oracle import render64 as R64
 from paper_2510_03312_gb300 import scenes as S
 
@@ -94,7 +95,48 @@ def test_skew_rotation_determinant():
     assert dev < 1e-7
 
 
-@pytest.mark.parametrize("N,mode", [(6, 0), (7, 0), (6, 1), (7, 1), (4, 0)])
+def test_cayley_rotation_is_the_rotation_by_twice_atan():
+    """The Cayley transform of A(omega) is a proper rotation about omega by
+    the angle 2 atan |omega| (the Gibbs-vector form), checked against SciPy's
+    rotation-vector map."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(3)
+    w = rng.normal(0, 0.8, (3, 40))
+    R = R64.rotation64(torch.tensor(w), S.ROT_CAYLEY).numpy()
+    n = np.linalg.norm(w, axis=0)
+    ref = Rotation.from_rotvec((w * (2 * np.arctan(n) / n)).T).as_matrix()
+    np.testing.assert_allclose(R, ref, atol=1e-13)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-13)
+
+
+def test_second_order_taylor_rotation():
+    """R = I + A + A^2/2: the matrix-product form, and within O(|omega|^3) of
+    the matrix exponential (SciPy's expm)."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(4)
+    w = rng.normal(0, 0.3, (3, 20))
+    R = R64.rotation64(torch.tensor(w), S.ROT_SKEW2).numpy()
+    for p in range(w.shape[1]):
+        o1, o2, o3 = w[:, p]
+        A = np.array([[0, -o3, o2], [o3, 0, -o1], [-o2, o1, 0]])
+        np.testing.assert_allclose(R[p], np.eye(3) + A + A @ A / 2, atol=1e-15)
+        assert np.abs(R[p] - expm(A)).max() <= np.linalg.norm(w[:, p]) ** 3 / 6 + 1e-15
+        small = 1e-2 * A
+        Rs = R64.rotation64(torch.tensor(1e-2 * w[:, p:p + 1]), S.ROT_SKEW2).numpy()[0]
+        assert np.abs(Rs - expm(small)).max() <= 1e-6 * np.linalg.norm(w[:, p]) ** 3
+
+
+@pytest.mark.parametrize("mode", [S.ROT_SKEW1, S.ROT_SKEW2, S.ROT_CAYLEY])
+def test_float32_rotation_closed_forms_match_float64(mode):
+    """The decision stage's entry-by-entry float32 rotation against the
+    float64 definitions (I + A, the product form, the linear solve)."""
+    sc = S.make_scene(11, 3, 300, rot_mode=mode)
+    r64 = R64.rotation64(torch.tensor(sc.plane("rot").astype(np.float64)), mode).numpy()
+    r32 = np.array(fp32_spec.rotation(sc), dtype=np.float64).transpose(2, 0, 1)
+    np.testing.assert_allclose(r32, r64, rtol=0, atol=4e-7)
+
+
+@pytest.mark.parametrize("N,mode", [(6, 0), (7, 0), (6, 1), (7, 1), (4, 0), (6, 2), (7, 3)])
 def test_sigma_blocks_match_appendix_closed_form(N, mode):
     """Sigma = L L^T has the block form printed in the appendix:
     [[R diag(s)^2 R^T, R diag(s) L_qx^T], [L_qx diag(s) R^T, L_qx L_qx^T + L_q L_q^T]],
