@@ -65,7 +65,13 @@ typedef enum {
   UBS_ERR_WORKSPACE = 7    /* workspace smaller than ubs_workspace_size */
 } ubs_status;
 
-enum { UBS_ROT_QUAT = 0, UBS_ROT_SKEW1 = 1 };
+/* Spatial rotation R_x of the spatial-orthogonal Cholesky factor (Sec. 4.2 and
+ * the appendix's table of rotation parameterisations): the normalised 3DGS
+ * quaternion, or from omega with the skew matrix A(omega) = [[0,-w3,w2],
+ * [w3,0,-w1],[-w2,w1,0]]: R = I + A (first-order Taylor of exp A, the paper's
+ * choice), R = I + A + A^2/2 (second-order Taylor) or the Cayley transform
+ * R = (I - A)^-1 (I + A) = I + 2 (A + A^2) / (1 + |omega|^2). */
+enum { UBS_ROT_QUAT = 0, UBS_ROT_SKEW1 = 1, UBS_ROT_SKEW2 = 2, UBS_ROT_CAYLEY = 3 };
 
 enum {
   UBS_FLAG_TIGHT_CUT = 1, /* cut each footprint at r_cut = 1-(a_min/o(q))^(1/beta_x) */
@@ -84,7 +90,8 @@ enum {
  *   mean_q  [C][P]        query mean mu_q; rows ordered q = [t, d] (N=7),
  *                         [d] (N=6), [t] (N=4); unused for N=3 (may be NULL)
  *   rot     [4][P] quaternion (w,x,y,z), normalised inside (UBS_ROT_QUAT), or
- *           [3][P] omega with R = I + A(omega) (UBS_ROT_SKEW1, Sec. 4.2)
+ *           [3][P] omega of A(omega) (UBS_ROT_SKEW1, UBS_ROT_SKEW2,
+ *           UBS_ROT_CAYLEY; Sec. 4.2)
  *   scale_x [3][P]        spatial scales s_x > 0
  *   L_qx    [3C][P]       C x 3 cross block, row-major: (k, j) at row 3k + j
  *   L_q     [C(C+1)/2][P] lower-triangular query block, packed row-major:
@@ -95,7 +102,7 @@ enum {
  *   rgb     [3][P]        colour                                          */
 typedef struct {
   int32_t N;        /* 3, 4, 6 or 7 */
-  int32_t rot_mode; /* UBS_ROT_QUAT or UBS_ROT_SKEW1 */
+  int32_t rot_mode; /* UBS_ROT_* */
   int64_t P;        /* number of primitives, >= 0 */
   const float* mean_x;
   const float* mean_q;

@@ -24,7 +24,8 @@
 //   L^ = chol(Sigma_q)             dSigma_q += L^{-T} Phi(L^T dL^) L^{-1}
 //                                  (Phi: lower triangle, halved diagonal)
 //   Sigma_q = L_qx L_qx^T + L_q L_q^T,  Sigma_qx = L_qx M^T,  Sigma_x = M M^T,
-//   M = R diag(s_x), R from the normalised quaternion or R = I + A(omega).
+//   M = R diag(s_x), R from the normalised quaternion or from A(omega):
+//   I + A, I + A + A^2/2 or the Cayley transform (I - A)^-1 (I + A).
 #pragma once
 
 #include "prim_forward.cuh"
@@ -370,9 +371,33 @@ UBS_HD void prim_backward_final(const PrimIn<C>& in, const PrimVI<C>& vi, int ro
     out.rot[2] = (gy - y * dot) / n;
     out.rot[3] = (gz - z * dot) / n;
   } else {
-    out.rot[0] = gR[7] - gR[5];
-    out.rot[1] = gR[2] - gR[6];
-    out.rot[2] = gR[3] - gR[1];
+    // through A(omega): L_k = sum_ij gR_ij dA_ij/domega_k
+    const float L[3] = {gR[7] - gR[5], gR[2] - gR[6], gR[3] - gR[1]};
+    if (rot_mode == 1) {
+      for (int k = 0; k < 3; ++k) out.rot[k] = L[k];
+    } else {
+      // R = I + l A + k A^2: through A^2, Q_k = sum_ij gR_ij d(A^2)_ij/domega_k
+      //   = (gR o)_k + (gR^T o)_k - 2 o_k tr(gR)
+      const float o[3] = {in.rot[0], in.rot[1], in.rot[2]};
+      const float tr = gR[0] + gR[4] + gR[8];
+      float Q[3];
+      for (int k = 0; k < 3; ++k)
+        Q[k] = (gR[3 * k] * o[0] + gR[3 * k + 1] * o[1] + gR[3 * k + 2] * o[2]) +
+               (gR[k] * o[0] + gR[3 + k] * o[1] + gR[6 + k] * o[2]) - 2.0f * o[k] * tr;
+      if (rot_mode == 2) {
+        for (int k = 0; k < 3; ++k) out.rot[k] = L[k] + 0.5f * Q[k];
+      } else {
+        // Cayley: k = l = c = 2 / (1 + |o|^2), dc/do_k = -c^2 o_k, and
+        // <gR, A + A^2> = sum_k o_k L_k + o^T gR o - |o|^2 tr(gR)
+        const float n = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+        const float c = 2.0f / (1.0f + n);
+        float oGo = 0.0f;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) oGo += o[i] * gR[3 * i + j] * o[j];
+        const float inner = (o[0] * L[0] + o[1] * L[1] + o[2] * L[2]) + oGo - n * tr;
+        for (int k = 0; k < 3; ++k) out.rot[k] = c * (L[k] + Q[k]) - c * c * o[k] * inner;
+      }
+    }
     out.rot[3] = 0.0f;
   }
   for (int i = 0; i < 3; ++i) {

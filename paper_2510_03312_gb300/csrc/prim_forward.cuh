@@ -82,11 +82,35 @@ UBS_HD void rotation_spec(const float* rot, int rot_mode, float* R) {
     R[6] = 2.0f * (x * z - w * y);
     R[7] = 2.0f * (y * z + w * x);
     R[8] = 1.0f - 2.0f * (x * x + y * y);
-  } else {
+  } else if (rot_mode == 1) {
     float o1 = rot[0], o2 = rot[1], o3 = rot[2];
     R[0] = 1.0f; R[1] = -o3;  R[2] = o2;
     R[3] = o3;   R[4] = 1.0f; R[5] = -o1;
     R[6] = -o2;  R[7] = o1;   R[8] = 1.0f;
+  } else {
+    // R = I + l A + k A^2 with (A^2)_ij = o_i o_j - delta_ij |o|^2: k = 1/2,
+    // l = 1 (second-order Taylor of exp A) or k = l = 2 / (1 + |o|^2) (the
+    // Cayley transform (I - A)^-1 (I + A) in closed form)
+    const float o1 = rot[0], o2 = rot[1], o3 = rot[2];
+    const float a11 = o1 * o1, a22 = o2 * o2, a33 = o3 * o3;
+    const float a12 = o1 * o2, a13 = o1 * o3, a23 = o2 * o3;
+    float k, l;
+    if (rot_mode == 2) {
+      k = 0.5f;
+      l = 1.0f;
+    } else {
+      k = 2.0f / (1.0f + ((a11 + a22) + a33));
+      l = k;
+    }
+    R[0] = 1.0f - k * (a22 + a33);
+    R[1] = k * a12 - l * o3;
+    R[2] = k * a13 + l * o2;
+    R[3] = k * a12 + l * o3;
+    R[4] = 1.0f - k * (a11 + a33);
+    R[5] = k * a23 - l * o1;
+    R[6] = k * a13 - l * o2;
+    R[7] = k * a23 + l * o1;
+    R[8] = 1.0f - k * (a11 + a22);
   }
 }
 
