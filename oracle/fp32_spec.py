@@ -151,9 +151,16 @@ def prim_stage(scene):
     pl = _planes(scene)
     C = scene.C
     P = scene.P
-    R = rotation(scene)
     s = pl["scale_x"]
-    M = [[R[i][j] * s[j] for j in range(3)] for i in range(3)]
+    if scene.rot_mode == 4:
+        # the plain Cholesky row: M is the factor itself, no arithmetic
+        lo = pl["rot"]
+        zero = np.zeros_like(s[0])
+        M = [[s[0], zero, zero], [lo[0], s[1], zero], [lo[1], lo[2], s[2]]]
+        R = None
+    else:
+        R = rotation(scene)
+        M = [[R[i][j] * s[j] for j in range(3)] for i in range(3)]
     Sx = {}
     for i in range(3):
         for j in range(i, 3):

@@ -100,11 +100,25 @@ def rotation64(rot, rot_mode):
     raise ValueError(f"rotation mode {rot_mode}")
 
 
+def spatial_factor64(leaves, rot_mode):
+    """[P, 3, 3] spatial block of L: R_x diag(s_x) (Sec. 4.2), or, for the
+    appendix's plain Cholesky row (rot_mode 4), the lower-triangular factor
+    with diagonal s_x and strictly-lower entries (l10, l20, l21) = rot."""
+    s = leaves["scale_x"].T                       # [P, 3]
+    if rot_mode == 4:
+        l10, l20, l21 = leaves["rot"][0], leaves["rot"][1], leaves["rot"][2]
+        zero = torch.zeros_like(l10)
+        rows = [torch.stack([s[:, 0], zero, zero], -1), torch.stack([l10, s[:, 1], zero], -1),
+                torch.stack([l20, l21, s[:, 2]], -1)]
+        return torch.stack(rows, -2)
+    R = rotation64(leaves["rot"], rot_mode)
+    return R * s[:, None, :]                     # R diag(s)
+
+
 def build_L(leaves, N, rot_mode):
     """[P, N, N] spatial-orthogonal Cholesky factor (Sec. 4.2)."""
-    R = rotation64(leaves["rot"], rot_mode)
-    s = leaves["scale_x"].T                       # [P, 3]
-    top_left = R * s[:, None, :]                 # R diag(s)
+    top_left = spatial_factor64(leaves, rot_mode)
+    s = leaves["scale_x"].T
     C = N - 3
     P = s.shape[0]
     if C == 0:

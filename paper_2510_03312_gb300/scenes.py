@@ -15,7 +15,9 @@ Layout (all float32, structure of arrays, one plane per scalar, stride P):
                                         [d] (N=6), [t] (N=4)
     rot           4 (quat) / 3 (skew)   quaternion (w, x, y, z), not normalised,
                                         or omega of the skew matrix A(omega)
-                                        (first- or second-order Taylor, Cayley)
+                                        (first- or second-order Taylor, Cayley),
+                                        or the strictly-lower entries
+                                        (l10, l20, l21) of a Cholesky factor
     scale_x       3                     spatial scales s_x > 0
     L_qx          3C                    C x 3 block, row-major (k, j) -> 3k + j
     L_q           C(C+1)/2              lower-triangular block, packed row-major
@@ -38,7 +40,10 @@ ROT_QUAT = 0
 ROT_SKEW1 = 1   # R = I + A(omega), the paper's first-order Taylor
 ROT_SKEW2 = 2   # R = I + A + A^2 / 2, second-order Taylor
 ROT_CAYLEY = 3  # R = (I - A)^-1 (I + A), the Cayley transform
-ROT_MODES = (ROT_QUAT, ROT_SKEW1, ROT_SKEW2, ROT_CAYLEY)
+ROT_CHOL = 4    # no rotation: the spatial block of L is a general lower-triangular
+                # factor, rot = its strictly-lower entries (l10, l20, l21),
+                # scale_x = its diagonal
+ROT_MODES = (ROT_QUAT, ROT_SKEW1, ROT_SKEW2, ROT_CAYLEY, ROT_CHOL)
 
 PLANE_ORDER = ("mean_x", "mean_q", "rot", "scale_x", "L_qx", "L_q", "b", "opacity", "rgb")
 
@@ -162,6 +167,9 @@ def make_scene(seed: int, N: int, P: int, *, means: str = "uniform", extent: flo
     if rot_mode == ROT_QUAT:
         q = rng.standard_normal((4, P))
         rot = q / np.linalg.norm(q, axis=0, keepdims=True)
+    elif rot_mode == ROT_CHOL:
+        # strictly-lower entries (l10, l20, l21) scaled by their row's diagonal
+        rot = sx[[1, 2, 2]] * rng.uniform(-0.5, 0.5, size=(3, P))
     else:
         rot = rng.normal(0.0, 0.3, size=(3, P))
     op = 1.0 / (1.0 + np.exp(-rng.standard_normal(P)))

@@ -126,6 +126,21 @@ def test_second_order_taylor_rotation():
         assert np.abs(Rs - expm(small)).max() <= 1e-6 * np.linalg.norm(w[:, p]) ** 3
 
 
+def test_plain_cholesky_factor_is_recovered_by_cholesky():
+    """The table's plain Cholesky row: Sigma_x = L L^T with L lower-triangular
+    (diagonal s_x, strictly-lower rot), so NumPy's Cholesky factorisation of
+    the oracle's Sigma_x returns those entries."""
+    sc = S.make_scene(12, 3, 50, rot_mode=S.ROT_CHOL)
+    leaves = R64.scene_leaves(sc)
+    L = R64.build_L(leaves, 3, S.ROT_CHOL)
+    Sx = (L @ L.transpose(-1, -2)).numpy()
+    ch = np.linalg.cholesky(Sx)
+    s, lo = sc.plane("scale_x").astype(np.float64), sc.plane("rot").astype(np.float64)
+    np.testing.assert_allclose(ch[:, [0, 1, 2], [0, 1, 2]], s.T, rtol=1e-12)
+    np.testing.assert_allclose(ch[:, [1, 2, 2], [0, 0, 1]], lo.T, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(ch[:, [0, 0, 1], [1, 2, 2]], 0.0)
+
+
 @pytest.mark.parametrize("mode", [S.ROT_SKEW1, S.ROT_SKEW2, S.ROT_CAYLEY])
 def test_float32_rotation_closed_forms_match_float64(mode):
     """The decision stage's entry-by-entry float32 rotation against the
@@ -136,7 +151,7 @@ def test_float32_rotation_closed_forms_match_float64(mode):
     np.testing.assert_allclose(r32, r64, rtol=0, atol=4e-7)
 
 
-@pytest.mark.parametrize("N,mode", [(6, 0), (7, 0), (6, 1), (7, 1), (4, 0), (6, 2), (7, 3)])
+@pytest.mark.parametrize("N,mode", [(6, 0), (7, 0), (6, 1), (7, 1), (4, 0), (6, 2), (7, 3), (6, 4)])
 def test_sigma_blocks_match_appendix_closed_form(N, mode):
     """Sigma = L L^T has the block form printed in the appendix:
     [[R diag(s)^2 R^T, R diag(s) L_qx^T], [L_qx diag(s) R^T, L_qx L_qx^T + L_q L_q^T]],
@@ -147,7 +162,6 @@ def test_sigma_blocks_match_appendix_closed_form(N, mode):
     R64.condition(lv, N, mode, _view_at(np.eye(3), [0, 0, 3]), terms)
     Sig = terms["Sigma"].numpy()
     C = N - 3
-    R = R64.rotation64(lv["rot"], mode).numpy()
     s = sc.plane("scale_x").T.astype(np.float64)
     lqx = sc.plane("L_qx").T.astype(np.float64).reshape(-1, C, 3)
     lq = np.zeros((sc.P, C, C))
@@ -155,8 +169,16 @@ def test_sigma_blocks_match_appendix_closed_form(N, mode):
     for i in range(C):
         for j in range(i + 1):
             lq[:, i, j] = pk[i * (i + 1) // 2 + j]
-    Rs = R * s[:, None, :]
-    np.testing.assert_allclose(Sig[:, :3, :3], np.einsum("pij,pj,pkj->pik", R, s * s, R), atol=1e-14)
+    if mode == S.ROT_CHOL:  # the plain Cholesky row: the spatial block is the factor itself
+        lo = sc.plane("rot").T.astype(np.float64)
+        Rs = np.zeros((sc.P, 3, 3))
+        Rs[:, [0, 1, 2], [0, 1, 2]] = s
+        Rs[:, [1, 2, 2], [0, 0, 1]] = lo
+        np.testing.assert_allclose(Sig[:, :3, :3], Rs @ Rs.transpose(0, 2, 1), atol=1e-14)
+    else:
+        R = R64.rotation64(lv["rot"], mode).numpy()
+        Rs = R * s[:, None, :]
+        np.testing.assert_allclose(Sig[:, :3, :3], np.einsum("pij,pj,pkj->pik", R, s * s, R), atol=1e-14)
     np.testing.assert_allclose(Sig[:, :3, 3:], Rs @ lqx.transpose(0, 2, 1), atol=1e-14)
     np.testing.assert_allclose(Sig[:, 3:, :3], lqx @ Rs.transpose(0, 2, 1), atol=1e-14)
     np.testing.assert_allclose(Sig[:, 3:, 3:], lqx @ lqx.transpose(0, 2, 1) + lq @ lq.transpose(0, 2, 1),
