@@ -346,13 +346,22 @@ UBS_HD void prim_backward_final(const PrimIn<C>& in, const PrimVI<C>& vi, int ro
       gM[i][j] += s;
     }
   float gR[9];
-  for (int j = 0; j < 3; ++j) {
-    float s = 0.0f;
-    for (int i = 0; i < 3; ++i) {
-      gR[3 * i + j] = gM[i][j] * in.s[j];
-      s += gM[i][j] * vi.R[3 * i + j];
+  if (rot_mode == 4) {
+    // the plain Cholesky row: M is the factor (diagonal s_x, strictly-lower rot)
+    for (int j = 0; j < 3; ++j) out.s[j] = gM[j][j];
+    out.rot[0] = gM[1][0];
+    out.rot[1] = gM[2][0];
+    out.rot[2] = gM[2][1];
+    out.rot[3] = 0.0f;
+  } else {
+    for (int j = 0; j < 3; ++j) {
+      float s = 0.0f;
+      for (int i = 0; i < 3; ++i) {
+        gR[3 * i + j] = gM[i][j] * in.s[j];
+        s += gM[i][j] * vi.R[3 * i + j];
+      }
+      out.s[j] = s;
     }
-    out.s[j] = s;
   }
   if (rot_mode == 0) {
     const float qw = in.rot[0], qx = in.rot[1], qy = in.rot[2], qz = in.rot[3];
@@ -370,7 +379,7 @@ UBS_HD void prim_backward_final(const PrimIn<C>& in, const PrimVI<C>& vi, int ro
     out.rot[1] = (gx - x * dot) / n;
     out.rot[2] = (gy - y * dot) / n;
     out.rot[3] = (gz - z * dot) / n;
-  } else {
+  } else if (rot_mode != 4) {
     // through A(omega): L_k = sum_ij gR_ij dA_ij/domega_k
     const float L[3] = {gR[7] - gR[5], gR[2] - gR[6], gR[3] - gR[1]};
     if (rot_mode == 1) {

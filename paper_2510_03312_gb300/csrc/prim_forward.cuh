@@ -116,9 +116,16 @@ UBS_HD void rotation_spec(const float* rot, int rot_mode, float* R) {
 
 template <int C>
 UBS_HD void prim_stage(const PrimIn<C>& in, int rot_mode, PrimVI<C>& vi) {
-  rotation_spec(in.rot, rot_mode, vi.R);
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) vi.M[3 * i + j] = vi.R[3 * i + j] * in.s[j];
+  if (rot_mode == 4) {
+    // the plain Cholesky row: M is the lower-triangular factor itself
+    vi.M[0] = in.s[0];  vi.M[1] = 0.0f;      vi.M[2] = 0.0f;
+    vi.M[3] = in.rot[0]; vi.M[4] = in.s[1];  vi.M[5] = 0.0f;
+    vi.M[6] = in.rot[1]; vi.M[7] = in.rot[2]; vi.M[8] = in.s[2];
+  } else {
+    rotation_spec(in.rot, rot_mode, vi.R);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) vi.M[3 * i + j] = vi.R[3 * i + j] * in.s[j];
+  }
   const float* M = vi.M;
   float Sx[6];
   for (int i = 0; i < 3; ++i)
