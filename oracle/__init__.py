@@ -28,6 +28,9 @@ Modules
                float64 autograd gradient, and the Adam step on raw
                parameters with the activation chain, the opacity and scale
                penalties and the spatial noise.
+``mcmc64``     MCMC relocation (Sec. 4.5 primitive management): dead
+               primitives moved onto live ones drawn by opacity with exact
+               integer weights, cloned opacity 1 - (1 - o)^(1/N).
 
 Every function names the passage it follows.  Parity status of each function
 is given in its module header.
