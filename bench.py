@@ -462,6 +462,25 @@ def bench_train(r, ds, wl, args, dev, pk, n_sm, flush):
             rows.append(evs)
     torch.cuda.synchronize()
     loss_last = float(loss_fn.loss[0])
+    # MCMC relocation (Sec. 4.5) with 1% of the primitives made dead first
+    reloc = TR.Relocator(opt)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    orow = reloc.opacity_row
+    dead = torch.rand(ds.P, device=dev, generator=gen) < 0.01
+    rand = torch.randint(-2 ** 63, 2 ** 63 - 1, (ds.P,), device=dev, dtype=torch.int64, generator=gen)
+    r_ms = []
+    for i in range(4):
+        with torch.no_grad():
+            opt.act[orow][dead] = 0.001
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        reloc(rand)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            r_ms.append(e0.elapsed_time(e1))
+    n_moved = int(reloc.n_relocated.item())
     stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(len(names))] for e in rows]).mean(0)
     with torch.no_grad():
         ds.params.copy_(params0)  # leave the scene as the other measurements found it
@@ -480,6 +499,7 @@ def bench_train(r, ds, wl, args, dev, pk, n_sm, flush):
         "MP_per_s": round(v.width * v.height / 1e6 / (step_ms * 1e-3), 2),
         "stage_ms": {n: round(float(m), 4) for n, m in zip(names, stage)},
         "loss_after_steps": round(loss_last, 6),
+        "mcmc_relocate": {"ms": round(float(np.median(r_ms)), 4), "relocated": n_moved, "primitives": ds.P},
         "roofline": {
             "image_loss": {"bound": "alu", "fp32_ops": loss_ops, "bytes": loss_bytes,
                            "achieved": round(loss_ops / t_loss / 1e12, 3), "peak": round(alu_peak, 2),

@@ -17,8 +17,9 @@
  *                   primitive parameter (differentiable rendering, Sec. 4.5)
  *
  * and the training step around it: ubs_image_loss (the image loss of
- * Sec. 4.5 and its gradient) and ubs_adam_step (the optimiser of Sec. 5.1
- * with the penalties and noise of Sec. 4.5).
+ * Sec. 4.5 and its gradient), ubs_adam_step (the optimiser of Sec. 5.1
+ * with the penalties and noise of Sec. 4.5) and ubs_mcmc_relocate (the
+ * primitive management of Sec. 4.5).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -310,6 +311,29 @@ typedef struct {
 ubs_status ubs_adam_step(int32_t K, int64_t P, const ubs_adam_plane* planes, const ubs_adam_config* cfg,
                          float* raw, float* act_out, const float* grad, float* m, float* v, const float* noise,
                          cudaStream_t stream);
+
+/* MCMC relocation of dead primitives (Sec. 4.5 primitive management, the
+ * kernel-agnostic scheme of Deformable Beta Splatting).  A primitive is dead
+ * when its opacity act[opacity_row] <= dead_threshold (3DGS-MCMC: 0.005).
+ * Each dead slot j is moved onto a live source drawn with probability
+ * proportional to opacity, exactly: live weights are the integers
+ * floor(o * 2^24), and the source is the first primitive whose inclusive
+ * cumulative weight exceeds rand[j] mod (total weight).  A source drawn n
+ * times and its n copies take the opacity 1 - (1 - o)^(1/(n+1)) (Sec. 4.5),
+ * which keeps their composited density; every other row of act and raw is
+ * copied from the source, and m and v of every touched primitive are
+ * zeroed.  Nothing moves when no primitive is alive.
+ * act, raw, m, v: device [K][P] planes (the layout of ubs_adam_step; raw of
+ *   the opacity row is its logit), 4-byte aligned, updated in place.
+ * rand: device uint64 [P], drawn by the caller, 8-byte aligned.
+ * sources: device int32 [P] or NULL: the source of each slot (-1: kept).
+ * n_relocated: device int64 or NULL: the number of slots moved.
+ * workspace: device, 256-byte aligned, >= ubs_mcmc_workspace_size(P).
+ * Asynchronous on `stream`; allocates nothing. */
+size_t ubs_mcmc_workspace_size(int64_t P);
+ubs_status ubs_mcmc_relocate(int32_t K, int64_t P, int32_t opacity_row, float dead_threshold, float* act,
+                             float* raw, float* m, float* v, const uint64_t* rand, int32_t* sources,
+                             int64_t* n_relocated, void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /* Forward rendering that allocates nothing.  (The paper has no counterpart:
  * this serves callers that cannot allocate device memory when they render,

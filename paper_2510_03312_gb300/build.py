@@ -30,6 +30,7 @@ UNITS = {
     "abi.cu": [],
     "noalloc.cu": [],
     "train.cu": [],
+    "mcmc.cu": [],
 }
 
 

@@ -1,7 +1,8 @@
-"""The training step around the rasterizer (Sec. 4.5 loss, Sec. 5.1 optimiser),
-as PyTorch plumbing over the C-ABI calls ``ubs_image_loss`` and
-``ubs_adam_step``: device buffers, the per-plane optimiser table and the
-order of the calls.  All arithmetic runs in libubs.so.
+"""The training step around the rasterizer (Sec. 4.5 loss, Sec. 5.1 optimiser,
+Sec. 4.5 primitive management), as PyTorch plumbing over the C-ABI calls
+``ubs_image_loss``, ``ubs_adam_step`` and ``ubs_mcmc_relocate``: device
+buffers, the per-plane optimiser table and the order of the calls.  All
+arithmetic runs in libubs.so.
 
 The optimiser keeps raw parameters; the rasterizer reads the activated ones
 (``DeviceScene.params``): opacity = sigmoid(raw), spatial scales and the
@@ -138,6 +139,39 @@ class Adam:
                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         if st != U.UBS_OK:
             raise U.UBSError(st, "ubs_adam_step")
+
+
+DEAD_THRESHOLD = 0.005  # 3DGS-MCMC's dead opacity, on which the DBS scheme builds
+
+
+class Relocator:
+    """ubs_mcmc_relocate on an ``Adam``'s buffers (Sec. 4.5 primitive
+    management): dead primitives move onto live ones drawn by opacity."""
+
+    def __init__(self, opt: "Adam", threshold: float = DEAD_THRESHOLD):
+        self.opt = opt
+        self.threshold = float(threshold)
+        rows = [k for k, (_, a, _, _) in enumerate(opt.table) if a == U.UBS_ACT_SIGMOID]
+        if len(rows) != 1:
+            raise ValueError("expected exactly one opacity plane")
+        self.opacity_row = rows[0]
+        n = U.ubs_mcmc_workspace_size(opt.P)
+        self._ws = torch.empty(n + 256, dtype=torch.uint8, device=opt.act.device)
+        self.ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.ws_bytes = n
+        self.sources = torch.empty(opt.P, dtype=torch.int32, device=opt.act.device)
+        self.n_relocated = torch.zeros(1, dtype=torch.int64, device=opt.act.device)
+
+    def __call__(self, rand: torch.Tensor):
+        """rand: [P] int64 tensor of random bits (read as uint64)."""
+        o = self.opt
+        st = U.ubs_mcmc_relocate(o.K, o.P, self.opacity_row, self.threshold, o.act.data_ptr(), o.raw.data_ptr(),
+                                 o.m.data_ptr(), o.v.data_ptr(), rand.data_ptr(), self.sources.data_ptr(),
+                                 self.n_relocated.data_ptr(), self.ws_ptr, self.ws_bytes,
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if st != U.UBS_OK:
+            raise U.UBSError(st, "ubs_mcmc_relocate")
+        return self.sources, self.n_relocated
 
 
 def train_step(r, loss_fn: ImageLoss, opts, target: torch.Tensor, dL: torch.Tensor, noises=None):

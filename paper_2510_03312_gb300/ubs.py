@@ -103,6 +103,9 @@ SIGNATURES = {
                                  c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "ubs_adam_step": (c_int32, [c_int32, c_int64, POINTER(ubs_adam_plane), POINTER(ubs_adam_config), c_void_p,
                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ubs_mcmc_workspace_size": (c_size_t, [c_int64]),
+    "ubs_mcmc_relocate": (c_int32, [c_int32, c_int64, c_int32, c_float, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
 }
 
 _lib = None
@@ -201,3 +204,13 @@ def ubs_image_loss(widths, heights, image, target, lambda_ssim, dL_dimage, loss,
 def ubs_adam_step(K, P, planes, cfg, raw, act_out, grad, m, v, noise, stream) -> int:
     return int(load().ubs_adam_step(int(K), int(P), planes, ctypes.byref(cfg), raw, act_out, grad, m, v, noise,
                                     stream))
+
+
+def ubs_mcmc_workspace_size(P) -> int:
+    return int(load().ubs_mcmc_workspace_size(int(P)))
+
+
+def ubs_mcmc_relocate(K, P, opacity_row, dead_threshold, act, raw, m, v, rand, sources, n_relocated, workspace,
+                      workspace_bytes, stream) -> int:
+    return int(load().ubs_mcmc_relocate(int(K), int(P), int(opacity_row), float(dead_threshold), act, raw, m, v,
+                                        rand, sources, n_relocated, workspace, workspace_bytes, stream))

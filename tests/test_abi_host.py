@@ -164,3 +164,29 @@ def test_adam_step_rejects_bad_arguments_before_launching(lib):
     planes[1].activation = U.UBS_ACT_SIGMOID
     planes[0].noise_row = 0
     assert call(noise=None) == U.UBS_ERR_INVALID_ARG
+
+
+def test_mcmc_workspace_and_argument_checks(lib):
+    P = 5000
+    nb = (P + 1023) // 1024
+    want = 256 + ((P * 8 + 255) // 256) * 256 + ((nb * 8 + 255) // 256) * 256 + 2 * ((P * 4 + 255) // 256) * 256
+    assert U.ubs_mcmc_workspace_size(P) == want
+    assert U.ubs_mcmc_workspace_size(0) == 0
+    fake = 0x10000
+    ws = U.ubs_mcmc_workspace_size(P)
+    ok = dict(K=15, P=P, opacity_row=13, dead_threshold=0.005, act=fake, raw=fake + 0x1000, m=fake + 0x2000,
+              v=fake + 0x3000, rand=fake + 0x4000, sources=None, n_relocated=None, workspace=fake,
+              workspace_bytes=ws, stream=None)
+
+    def call(**kw):
+        a = dict(ok)
+        a.update(kw)
+        return U.ubs_mcmc_relocate(**a)
+
+    assert call(K=0) == U.UBS_ERR_INVALID_ARG
+    assert call(opacity_row=15) == U.UBS_ERR_INVALID_ARG
+    assert call(dead_threshold=1.0) == U.UBS_ERR_INVALID_ARG
+    assert call(rand=None) == U.UBS_ERR_INVALID_ARG
+    assert call(rand=fake + 4) == U.UBS_ERR_ALIGNMENT
+    assert call(workspace=fake + 64) == U.UBS_ERR_ALIGNMENT
+    assert call(workspace_bytes=ws - 1) == U.UBS_ERR_WORKSPACE
