@@ -141,6 +141,40 @@ class Adam:
             raise U.UBSError(st, "ubs_adam_step")
 
 
+def save_checkpoint(path: str, opts, iteration: int = 0) -> None:
+    """Writes the optimiser state of every scene (raw and activated
+    parameters, Adam moments, step count) to one .npz file, from which
+    training resumes where it stopped.  (Runs after a resume agree with an
+    uninterrupted one to float rounding, not bit for bit: the backward
+    blend's per-record sums are float atomics, whose order varies.)"""
+    arrays = {"iteration": np.array(iteration, dtype=np.int64), "n_scenes": np.array(len(opts), dtype=np.int64)}
+    for i, o in enumerate(opts):
+        arrays[f"raw{i}"] = o.raw.detach().cpu().numpy()
+        arrays[f"act{i}"] = o.act.detach().cpu().numpy()
+        arrays[f"m{i}"] = o.m.detach().cpu().numpy()
+        arrays[f"v{i}"] = o.v.detach().cpu().numpy()
+        arrays[f"step{i}"] = np.array(o.step_count, dtype=np.int64)
+    np.savez(path, **arrays)
+
+
+def load_checkpoint(path: str, opts) -> int:
+    """Restores what save_checkpoint wrote into optimisers of the same scene
+    layouts (in place, on their devices); returns the saved iteration."""
+    with np.load(path) as z:
+        if int(z["n_scenes"]) != len(opts):
+            raise ValueError("checkpoint holds a different number of scenes")
+        for i, o in enumerate(opts):
+            for name in ("raw", "act", "m", "v"):
+                a = z[f"{name}{i}"]
+                dst = getattr(o, name)
+                if tuple(a.shape) != tuple(dst.shape):
+                    raise ValueError(f"checkpoint {name}{i} has shape {a.shape}, expected {tuple(dst.shape)}")
+                with torch.no_grad():
+                    dst.copy_(torch.from_numpy(a))
+            o.step_count = int(z[f"step{i}"])
+        return int(z["iteration"])
+
+
 DEAD_THRESHOLD = 0.005  # 3DGS-MCMC's dead opacity, on which the DBS scheme builds
 
 

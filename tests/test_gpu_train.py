@@ -140,3 +140,42 @@ def test_training_steps_reduce_the_loss(dev):
         losses.append(float(TR.train_step(r, loss_fn, [opt], target, dL)[0]))
     assert np.all(np.isfinite(losses))
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_training_resumes_from_a_checkpoint(dev, tmp_path):
+    """Three steps, a checkpoint, two more steps; a fresh trainer loaded from
+    the checkpoint and run for the same two steps ends in the same state, to
+    the rounding left by the backward blend's float atomics (the loaded
+    state itself is bit-identical)."""
+    from paper_2510_03312_gb300 import raster
+    from paper_2510_03312_gb300 import train as TR
+    wl = S.workload_static_small(P=1500, size=64)
+    sc = wl.scenes[0]
+
+    def trainer():
+        ds = raster.DeviceScene.from_scene(sc, device=dev)
+        r = raster.Rasterizer([ds], wl.views, wl.cfg, device=dev)
+        r.forward(check=True)
+        return ds, r, TR.Adam(sc, ds.params), TR.ImageLoss(wl.views, device=dev)
+
+    target = torch.rand(3 * 64 * 64, device=dev)
+    noise = torch.randn(3, sc.P, device=dev) * 1e-4
+    ds, r, opt, lf = trainer()
+    dL = torch.empty_like(target)
+    for _ in range(3):
+        TR.train_step(r, lf, [opt], target, dL, [noise])
+    path = str(tmp_path / "ckpt.npz")
+    TR.save_checkpoint(path, [opt], iteration=3)
+    for _ in range(2):
+        TR.train_step(r, lf, [opt], target, dL, [noise])
+    torch.cuda.synchronize()
+    ds2, r2, opt2, lf2 = trainer()
+    assert TR.load_checkpoint(path, [opt2]) == 3
+    with np.load(path) as z:
+        assert np.array_equal(opt2.raw.cpu().numpy(), z["raw0"]) and opt2.step_count == 3
+    for _ in range(2):
+        TR.train_step(r2, lf2, [opt2], target, dL, [noise])
+    torch.cuda.synchronize()
+    for name in ("raw", "act", "m", "v"):
+        a, b = getattr(opt, name), getattr(opt2, name)
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-6), (name, float((a - b).abs().max()))

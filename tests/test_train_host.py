@@ -51,3 +51,23 @@ def test_raw_from_activated_inverts_the_activations():
         elif a == U.UBS_ACT_EXP:
             back[k] = torch.exp(raw[k])
     assert torch.allclose(back, act, rtol=1e-12, atol=1e-12)
+
+
+def test_checkpoint_round_trip(tmp_path):
+    sc = S.make_scene(9, 7, 40)
+    act = torch.tensor(sc.params)
+    a = TR.Adam(sc, act.clone())
+    a.m.normal_()
+    a.v.uniform_()
+    a.raw.add_(0.5)
+    a.step_count = 17
+    path = str(tmp_path / "ckpt.npz")
+    TR.save_checkpoint(path, [a], iteration=123)
+    b = TR.Adam(sc, act.clone())
+    assert TR.load_checkpoint(path, [b]) == 123
+    for name in ("raw", "act", "m", "v"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+    assert b.step_count == 17
+    other = TR.Adam(S.make_scene(9, 3, 40), torch.tensor(S.make_scene(9, 3, 40).params))
+    with pytest.raises(ValueError):
+        TR.load_checkpoint(path, [other])
