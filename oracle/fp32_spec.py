@@ -19,6 +19,13 @@ same written rules.  This module is the oracle's statement of those rules:
     log: x = m 2^e with m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1), then
          log m = 2 atanh(s) = s (2 + z (2/3 + z (2/5 + z (2/7 + z (2/9 +
          z 2/11))))) with z = s^2, and log x = e ln2_hi + (poly + e ln2_lo).
+    sin, cos (x >= 0): Cody & Waite reduction x = j pi/2 + r with j =
+         rint(x 2/pi) and pi/2 split into three parts (12, 12 and 24
+         significant bits), r = ((x - j P1) - j P2) - j P3; the Taylor
+         polynomials sin r = r + r (z (-1/3! + z (1/5! + z (-1/7! + z 1/9!))))
+         and cos r = 1 + z (-1/2! + z (1/4! + z (-1/6! + z (1/8! - z 1/10!))))
+         with z = r^2 and binary32-rounded coefficients; the quadrant j mod 4
+         picks (s, c), (c, -s), (-s, -c) or (-c, s).
   Both are within a few ulp of the true functions (tests pin this).
 
 The quantities follow the paper: Sec. 4.2 (L, Sigma blocks), Sec. 4.3
@@ -48,6 +55,15 @@ LN2_LO = F(float.fromhex("0x1.7f7d1cp-20"))    # ln 2 - LN2_HI rounded
 SQRT2 = F(float.fromhex("0x1.6a09e6p+0"))
 EXP_C = [F(1) / F(f) for f in (5040, 720, 120, 24, 6, 2, 1, 1)]   # 1/7! ... 1/0!
 LOG_C = [F(2) / F(k) for k in (11, 9, 7, 5, 3, 1)]                 # 2/11 ... 2/1
+# pi/2 = PIO2_A + PIO2_B + PIO2_C (12, 12, 24 significant bits), 2/pi, and the
+# alternating 1/k! of the sine (odd k) and cosine (even k) series
+TWO_OVER_PI = F(float.fromhex("0x1.45f306p-1"))
+PIO2_A = F(float.fromhex("0x1.92p+0"))
+PIO2_B = F(float.fromhex("0x1.fb4p-12"))
+PIO2_C = F(float.fromhex("0x1.4442d2p-24"))
+SIN_C = [F(float.fromhex(h)) for h in ("-0x1.555556p-3", "0x1.111112p-7", "-0x1.a01a02p-13", "0x1.71de3ap-19")]
+COS_C = [F(float.fromhex(h)) for h in ("-0x1p-1", "0x1.555556p-5", "-0x1.6c16c2p-10", "0x1.a01a02p-16",
+                                         "-0x1.27e4fcp-22")]
 MARG_R = F(float.fromhex("0x1.004p+0"))        # 1 + 2^-10
 MARG_A = F(float.fromhex("0x1p-6"))            # 2^-6 pixel
 
@@ -89,6 +105,26 @@ def log_spec(x):
     return np.where(bad, F(-np.inf), out).astype(F)
 
 
+def sincos_spec(x):
+    """(sin x, cos x) in binary32 for x >= 0 (Cody-Waite by pi/2, Taylor)."""
+    x = np.asarray(x, dtype=F)
+    j = np.rint(x * TWO_OVER_PI).astype(F)
+    r = ((x - j * PIO2_A) - j * PIO2_B) - j * PIO2_C
+    z = r * r
+    ps = SIN_C[3]
+    for c in (SIN_C[2], SIN_C[1], SIN_C[0]):
+        ps = c + z * ps
+    s = r + r * (z * ps)
+    pc = COS_C[4]
+    for c in (COS_C[3], COS_C[2], COS_C[1], COS_C[0]):
+        pc = c + z * pc
+    c = F(1) + z * pc
+    q = j.astype(np.int64) & 3
+    sin = np.select([q == 0, q == 1, q == 2], [s, c, -s], -c).astype(F)
+    cos = np.select([q == 0, q == 1, q == 2], [c, -s, -c], s).astype(F)
+    return sin, cos
+
+
 # ----------------------------------------------------------------------------
 # per-primitive, view-independent stage (Sec. 4.2 and the view-independent
 # part of Sec. 4.3)
@@ -108,7 +144,9 @@ def rotation(scene):
     a_ij = o_i o_j
         R = I + l A + k A^2,  (A^2)_ij = a_ij - delta_ij (a11 + a22 + a33),
     k = 1/2, l = 1 (second-order Taylor) or k = l = 2 / (1 + ((a11 + a22) + a33))
-    (Cayley: (I - A)^{-1}(I + A) in closed form), evaluated entry by entry as
+    (Cayley: (I - A)^{-1}(I + A) in closed form), or, for exp(A), Rodrigues'
+    l = sin t / t and k = (1 - cos t) / t^2 (t = |omega|; Taylor series in t^2
+    below t^2 = 1/4, else sincos_spec), evaluated entry by entry as
         R00 = 1 - k (a22 + a33)   R01 = k a12 - l o3   R02 = k a13 + l o2
         R10 = k a12 + l o3        R11 = 1 - k (a11 + a33)   R12 = k a23 - l o1
         R20 = k a13 - l o2        R21 = k a23 + l o1   R22 = 1 - k (a11 + a22)."""
@@ -127,7 +165,7 @@ def rotation(scene):
         o1, o2, o3 = rot[0], rot[1], rot[2]
         one = np.ones_like(o1)
         R = [[one, -o3, o2], [o3, one, -o1], [-o2, o1, one]]
-    elif scene.rot_mode in (2, 3):
+    elif scene.rot_mode in (2, 3, 5):
         o1, o2, o3 = rot[0], rot[1], rot[2]
         a11, a22, a33 = o1 * o1, o2 * o2, o3 * o3
         a12, a13, a23 = o1 * o2, o1 * o3, o2 * o3
@@ -135,9 +173,25 @@ def rotation(scene):
         if scene.rot_mode == 2:
             k = np.full_like(o1, F(0.5))
             l = np.ones_like(o1)
-        else:
+        elif scene.rot_mode == 3:
             k = F(2) / (one + ((a11 + a22) + a33))
             l = k
+        else:
+            # exp(A) (Rodrigues): l = sin t / t, k = (1 - cos t) / t^2 with t^2 = n;
+            # below n = 1/4 their Taylor series in n (Horner), else sincos_spec
+            n = (a11 + a22) + a33
+            s1, s2, s3, s4 = SIN_C
+            c2, c3, c4, c5 = COS_C[1:]
+            l_ser = one + n * (s1 + n * (s2 + n * (s3 + n * s4)))
+            k_ser = F(0.5) + n * (-c2 + n * (-c3 + n * (-c4 + n * -c5)))
+            t = np.sqrt(n)
+            sn, cs = sincos_spec(t)
+            small = n < F(0.25)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                l_big = sn / t
+                k_big = (one - cs) / n
+            l = np.where(small, l_ser, l_big).astype(F)
+            k = np.where(small, k_ser, k_big).astype(F)
         R = [[one - k * (a22 + a33), k * a12 - l * o3, k * a13 + l * o2],
              [k * a12 + l * o3, one - k * (a11 + a33), k * a23 - l * o1],
              [k * a13 - l * o2, k * a23 + l * o1, one - k * (a11 + a22)]]

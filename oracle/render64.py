@@ -78,8 +78,8 @@ def rotation64(rot, rot_mode):
     formula (Sec. 3); the skew-symmetric forms of the appendix on the
     spatial-orthogonal Cholesky parameterisation (its table of rotation
     parameterisations): R = I + A (first-order Taylor of exp A, the paper's
-    choice), R = I + A + A^2/2 (second-order Taylor) and the Cayley transform
-    R = (I - A)^{-1} (I + A), each written as its definition."""
+    choice), R = I + A + A^2/2 (second-order Taylor), the Cayley transform
+    R = (I - A)^{-1} (I + A) and R = exp(A), each written as its definition."""
     if rot_mode == 0:
         q = rot / torch.sqrt((rot * rot).sum(0, keepdim=True))
         w, x, y, z = q[0], q[1], q[2], q[3]
@@ -97,6 +97,8 @@ def rotation64(rot, rot_mode):
         return eye + A + 0.5 * (A @ A)
     if rot_mode == 3:
         return torch.linalg.solve(eye - A, eye + A)
+    if rot_mode == 5:
+        return torch.linalg.matrix_exp(A)
     raise ValueError(f"rotation mode {rot_mode}")
 
 

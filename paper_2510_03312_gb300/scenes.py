@@ -15,7 +15,8 @@ Layout (all float32, structure of arrays, one plane per scalar, stride P):
                                         [d] (N=6), [t] (N=4)
     rot           4 (quat) / 3 (skew)   quaternion (w, x, y, z), not normalised,
                                         or omega of the skew matrix A(omega)
-                                        (first- or second-order Taylor, Cayley),
+                                        (first- or second-order Taylor, Cayley,
+                                        matrix exponential),
                                         or the strictly-lower entries
                                         (l10, l20, l21) of a Cholesky factor
     scale_x       3                     spatial scales s_x > 0
@@ -43,7 +44,8 @@ ROT_CAYLEY = 3  # R = (I - A)^-1 (I + A), the Cayley transform
 ROT_CHOL = 4    # no rotation: the spatial block of L is a general lower-triangular
                 # factor, rot = its strictly-lower entries (l10, l20, l21),
                 # scale_x = its diagonal
-ROT_MODES = (ROT_QUAT, ROT_SKEW1, ROT_SKEW2, ROT_CAYLEY, ROT_CHOL)
+ROT_EXP = 5     # R = exp(A), the matrix exponential
+ROT_MODES = (ROT_QUAT, ROT_SKEW1, ROT_SKEW2, ROT_CAYLEY, ROT_CHOL, ROT_EXP)
 
 PLANE_ORDER = ("mean_x", "mean_q", "rot", "scale_x", "L_qx", "L_q", "b", "opacity", "rgb")
 

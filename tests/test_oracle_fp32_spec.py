@@ -54,7 +54,7 @@ def _small_workloads():
         out.append(S.Workload(f"n{N}", [sc], views))
     sk = S.make_scene(24, 3, 1500, means="uniform", extent=1.0, rot_mode=S.ROT_SKEW1)
     out.append(S.Workload("skew", [sk], S.workload_static_small().views))
-    for name, mode in (("skew2", S.ROT_SKEW2), ("cayley", S.ROT_CAYLEY), ("chol", S.ROT_CHOL)):
+    for name, mode in (("skew2", S.ROT_SKEW2), ("cayley", S.ROT_CAYLEY), ("chol", S.ROT_CHOL), ("exp", S.ROT_EXP)):
         sk = S.make_scene(25 + mode, 3, 1500, means="uniform", extent=1.0, rot_mode=mode)
         out.append(S.Workload(name, [sk], S.workload_static_small().views))
     return out

@@ -33,7 +33,8 @@ def _loss(orc, leaves, g):
     return float((img * g).sum())
 
 
-@pytest.mark.parametrize("N,mode", [(3, 0), (3, 1), (6, 0), (7, 1), (4, 0), (3, 2), (6, 3), (3, 4), (7, 4)])
+@pytest.mark.parametrize("N,mode", [(3, 0), (3, 1), (6, 0), (7, 1), (4, 0), (3, 2), (6, 3), (3, 4), (7, 4), (3, 5),
+                                    (6, 5)])
 def test_autograd_matches_central_differences(N, mode):
     sc, v, cfg = _tiny(N, mode, 40 + N + mode)
     orc = R64.Oracle([sc], [v], cfg)

@@ -141,7 +141,33 @@ def test_plain_cholesky_factor_is_recovered_by_cholesky():
     np.testing.assert_allclose(ch[:, [0, 0, 1], [1, 2, 2]], 0.0)
 
 
-@pytest.mark.parametrize("mode", [S.ROT_SKEW1, S.ROT_SKEW2, S.ROT_CAYLEY])
+def test_exponential_rotation_matches_scipy_expm():
+    """R = exp(A(omega)) against SciPy's expm, and a proper rotation."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(5)
+    w = rng.normal(0, 1.0, (3, 30))
+    R = R64.rotation64(torch.tensor(w), S.ROT_EXP).numpy()
+    for p in range(w.shape[1]):
+        o1, o2, o3 = w[:, p]
+        A = np.array([[0, -o3, o2], [o3, 0, -o1], [-o2, o1, 0]])
+        np.testing.assert_allclose(R[p], expm(A), atol=1e-13)
+    np.testing.assert_allclose(np.einsum("pji,pjk->pik", R, R), np.broadcast_to(np.eye(3), R.shape), atol=1e-13)
+
+
+def test_float32_sine_and_cosine():
+    """The decision stage's binary32 sin and cos against float64 libm."""
+    x = np.concatenate([np.linspace(0, 1, 20001), np.linspace(1, 200, 200001)]).astype(np.float32)
+    s, c = fp32_spec.sincos_spec(x)
+    xd = x.astype(np.float64)
+    assert np.abs(s.astype(np.float64) - np.sin(xd)).max() < 2.5e-7
+    assert np.abs(c.astype(np.float64) - np.cos(xd)).max() < 2.5e-7
+    small = x[(x > 0) & (x < 0.5)]
+    ss, _ = fp32_spec.sincos_spec(small)
+    rel = np.abs(ss.astype(np.float64) / np.sin(small.astype(np.float64)) - 1)
+    assert rel.max() < 3e-7
+
+
+@pytest.mark.parametrize("mode", [S.ROT_SKEW1, S.ROT_SKEW2, S.ROT_CAYLEY, S.ROT_EXP])
 def test_float32_rotation_closed_forms_match_float64(mode):
     """The decision stage's entry-by-entry float32 rotation against the
     float64 definitions (I + A, the product form, the linear solve)."""
@@ -151,7 +177,7 @@ def test_float32_rotation_closed_forms_match_float64(mode):
     np.testing.assert_allclose(r32, r64, rtol=0, atol=4e-7)
 
 
-@pytest.mark.parametrize("N,mode", [(6, 0), (7, 0), (6, 1), (7, 1), (4, 0), (6, 2), (7, 3), (6, 4)])
+@pytest.mark.parametrize("N,mode", [(6, 0), (7, 0), (6, 1), (7, 1), (4, 0), (6, 2), (7, 3), (6, 4), (7, 5)])
 def test_sigma_blocks_match_appendix_closed_form(N, mode):
     """Sigma = L L^T has the block form printed in the appendix:
     [[R diag(s)^2 R^T, R diag(s) L_qx^T], [L_qx diag(s) R^T, L_qx L_qx^T + L_q L_q^T]],
