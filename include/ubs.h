@@ -74,8 +74,10 @@ typedef enum {
  * R = (I - A)^-1 (I + A) = I + 2 (A + A^2) / (1 + |omega|^2).  UBS_ROT_CHOL is
  * the table's plain Cholesky row: no rotation, the spatial block of L is a
  * general lower-triangular factor with diagonal scale_x and strictly-lower
- * entries (l10, l20, l21) = rot. */
-enum { UBS_ROT_QUAT = 0, UBS_ROT_SKEW1 = 1, UBS_ROT_SKEW2 = 2, UBS_ROT_CAYLEY = 3, UBS_ROT_CHOL = 4 };
+ * entries (l10, l20, l21) = rot.  UBS_ROT_EXP is the table's matrix
+ * exponential R = exp(A(omega)) (Rodrigues' form; the decision stage takes
+ * sin and cos from the library's own binary32 functions). */
+enum { UBS_ROT_QUAT = 0, UBS_ROT_SKEW1 = 1, UBS_ROT_SKEW2 = 2, UBS_ROT_CAYLEY = 3, UBS_ROT_CHOL = 4, UBS_ROT_EXP = 5 };
 
 enum {
   UBS_FLAG_TIGHT_CUT = 1, /* cut each footprint at r_cut = 1-(a_min/o(q))^(1/beta_x) */
@@ -95,7 +97,7 @@ enum {
  *                         [d] (N=6), [t] (N=4); unused for N=3 (may be NULL)
  *   rot     [4][P] quaternion (w,x,y,z), normalised inside (UBS_ROT_QUAT), or
  *           [3][P] omega of A(omega) (UBS_ROT_SKEW1, UBS_ROT_SKEW2,
- *           UBS_ROT_CAYLEY; Sec. 4.2), or [3][P] (l10, l20, l21) of the
+ *           UBS_ROT_CAYLEY, UBS_ROT_EXP; Sec. 4.2), or [3][P] (l10, l20, l21) of the
  *           spatial Cholesky factor (UBS_ROT_CHOL)
  *   scale_x [3][P]        spatial scales s_x > 0
  *   L_qx    [3C][P]       C x 3 cross block, row-major: (k, j) at row 3k + j

@@ -28,7 +28,7 @@ bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 
 ubs_status check_scene(const ubs_scene& s) {
   if (!(s.N == 3 || s.N == 4 || s.N == 6 || s.N == 7)) return UBS_ERR_INVALID_ARG;
-  if (s.rot_mode < UBS_ROT_QUAT || s.rot_mode > UBS_ROT_CHOL) return UBS_ERR_INVALID_ARG;
+  if (s.rot_mode < UBS_ROT_QUAT || s.rot_mode > UBS_ROT_EXP) return UBS_ERR_INVALID_ARG;
   if (s.P < 0 || s.P > (int64_t)0x7fffffff) return UBS_ERR_INVALID_ARG;
   if (s.P == 0) return UBS_OK;
   const void* req[] = {s.mean_x, s.rot, s.scale_x, s.b, s.opacity, s.rgb};

@@ -25,7 +25,7 @@
 //                                  (Phi: lower triangle, halved diagonal)
 //   Sigma_q = L_qx L_qx^T + L_q L_q^T,  Sigma_qx = L_qx M^T,  Sigma_x = M M^T,
 //   M = R diag(s_x), R from the normalised quaternion or from A(omega):
-//   I + A, I + A + A^2/2 or the Cayley transform (I - A)^-1 (I + A).
+//   I + A, I + A + A^2/2, the Cayley transform (I - A)^-1 (I + A) or exp(A).
 #pragma once
 
 #include "prim_forward.cuh"
@@ -393,19 +393,38 @@ UBS_HD void prim_backward_final(const PrimIn<C>& in, const PrimVI<C>& vi, int ro
       for (int k = 0; k < 3; ++k)
         Q[k] = (gR[3 * k] * o[0] + gR[3 * k + 1] * o[1] + gR[3 * k + 2] * o[2]) +
                (gR[k] * o[0] + gR[3 + k] * o[1] + gR[6 + k] * o[2]) - 2.0f * o[k] * tr;
-      if (rot_mode == 2) {
-        for (int k = 0; k < 3; ++k) out.rot[k] = L[k] + 0.5f * Q[k];
-      } else {
-        // Cayley: k = l = c = 2 / (1 + |o|^2), dc/do_k = -c^2 o_k, and
-        // <gR, A + A^2> = sum_k o_k L_k + o^T gR o - |o|^2 tr(gR)
-        const float n = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
-        const float c = 2.0f / (1.0f + n);
-        float oGo = 0.0f;
-        for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) oGo += o[i] * gR[3 * i + j] * o[j];
-        const float inner = (o[0] * L[0] + o[1] * L[1] + o[2] * L[2]) + oGo - n * tr;
-        for (int k = 0; k < 3; ++k) out.rot[k] = c * (L[k] + Q[k]) - c * c * o[k] * inner;
+      // l, k and their derivatives in n = |o|^2: grad_k = l L_k + k Q_k +
+      // 2 o_k (l' <gR, A> + k' <gR, A^2>), <gR, A> = sum_k o_k L_k and
+      // <gR, A^2> = o^T gR o - n tr(gR)
+      const float n = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+      float l, kk, dl, dk;
+      if (rot_mode == 2) {  // second-order Taylor
+        l = 1.0f;
+        kk = 0.5f;
+        dl = dk = 0.0f;
+      } else if (rot_mode == 3) {  // Cayley: l = k = 2 / (1 + n), derivative -l^2 / 2
+        l = kk = 2.0f / (1.0f + n);
+        dl = dk = -0.5f * l * l;
+      } else if (n < 0.25f) {  // exp A, Taylor series in n
+        l = 1.0f + n * (spec::kInv3 + n * (spec::kInv5 + n * (spec::kInv7 + n * spec::kInv9)));
+        kk = 0.5f + n * (-spec::kInv4 + n * (-spec::kInv6 + n * (-spec::kInv8 + n * -spec::kInv10)));
+        dl = spec::kInv3 + n * (2.0f * spec::kInv5 + n * (3.0f * spec::kInv7 + n * 4.0f * spec::kInv9));
+        dk = -spec::kInv4 + n * (-2.0f * spec::kInv6 + n * (-3.0f * spec::kInv8 + n * -4.0f * spec::kInv10));
+      } else {  // exp A: l = sin t / t, k = (1 - cos t) / n, l' = (cos t - l) / (2n), k' = (l/2 - k) / n
+        const float t = sqrtf(n);
+        float s, c;
+        spec::sincos32(t, &s, &c);
+        l = s / t;
+        kk = (1.0f - c) / n;
+        dl = (c - l) / (2.0f * n);
+        dk = (0.5f * l - kk) / n;
       }
+      float oGo = 0.0f;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) oGo += o[i] * gR[3 * i + j] * o[j];
+      const float inA = o[0] * L[0] + o[1] * L[1] + o[2] * L[2];
+      const float inA2 = oGo - n * tr;
+      for (int k = 0; k < 3; ++k) out.rot[k] = l * L[k] + kk * Q[k] + 2.0f * o[k] * (dl * inA + dk * inA2);
     }
     out.rot[3] = 0.0f;
   }

@@ -89,8 +89,8 @@ UBS_HD void rotation_spec(const float* rot, int rot_mode, float* R) {
     R[6] = -o2;  R[7] = o1;   R[8] = 1.0f;
   } else {
     // R = I + l A + k A^2 with (A^2)_ij = o_i o_j - delta_ij |o|^2: k = 1/2,
-    // l = 1 (second-order Taylor of exp A) or k = l = 2 / (1 + |o|^2) (the
-    // Cayley transform (I - A)^-1 (I + A) in closed form)
+    // l = 1 (second-order Taylor of exp A), k = l = 2 / (1 + |o|^2) (the
+    // Cayley transform (I - A)^-1 (I + A) in closed form), or exp A itself
     const float o1 = rot[0], o2 = rot[1], o3 = rot[2];
     const float a11 = o1 * o1, a22 = o2 * o2, a33 = o3 * o3;
     const float a12 = o1 * o2, a13 = o1 * o3, a23 = o2 * o3;
@@ -98,9 +98,23 @@ UBS_HD void rotation_spec(const float* rot, int rot_mode, float* R) {
     if (rot_mode == 2) {
       k = 0.5f;
       l = 1.0f;
-    } else {
+    } else if (rot_mode == 3) {
       k = 2.0f / (1.0f + ((a11 + a22) + a33));
       l = k;
+    } else {
+      // exp(A) by Rodrigues: l = sin t / t, k = (1 - cos t) / t^2, t = |o|;
+      // below t^2 = 1/4 their Taylor series in t^2, else the rule set's sin, cos
+      const float n = (a11 + a22) + a33;
+      if (n < 0.25f) {
+        l = 1.0f + n * (spec::kInv3 + n * (spec::kInv5 + n * (spec::kInv7 + n * spec::kInv9)));
+        k = 0.5f + n * (-spec::kInv4 + n * (-spec::kInv6 + n * (-spec::kInv8 + n * -spec::kInv10)));
+      } else {
+        const float t = sqrtf(n);
+        float s, c;
+        spec::sincos32(t, &s, &c);
+        l = s / t;
+        k = (1.0f - c) / n;
+      }
     }
     R[0] = 1.0f - k * (a22 + a33);
     R[1] = k * a12 - l * o3;

@@ -18,6 +18,13 @@
 //           log m = 2 atanh(s) summed as s (2 + z(2/3 + z(2/5 + z(2/7 +
 //           z(2/9 + z 2/11))))) with z = s^2; log x = e ln2_hi + (poly +
 //           e ln2_lo); x <= 0 (or NaN) returns -inf.
+//      sin, cos (x >= 0): Cody & Waite reduction x = j pi/2 + r, j =
+//           rint(x 2/pi), with pi/2 split into three parts of at most 12
+//           significant bits each but the last, r = ((x - j P1) - j P2) -
+//           j P3; with z = r^2, sin r = r + r (z (-1/3! + z (1/5! + z (-1/7!
+//           + z 1/9!)))) and cos r = 1 + z (-1/2! + z (1/4! + z (-1/6! +
+//           z (1/8! - z 1/10!)))) (binary32-rounded coefficients); the
+//           quadrant j mod 4 picks (s, c), (c, -s), (-s, -c) or (-c, s).
 #pragma once
 
 #ifndef UBS_HD
@@ -76,6 +83,28 @@ UBS_HD float exp32(float x) {
   float scale = bits_to_float(((int32_t)k + 127) << 23);
   float out = p * scale;
   return under ? 0.0f : out;
+}
+
+// pi/2 = kPio2a + kPio2b + kPio2c (12, 12 and 24 significant bits)
+constexpr float kTwoOverPi = 0x1.45f306p-1f;
+constexpr float kPio2a = 0x1.92p+0f;
+constexpr float kPio2b = 0x1.fb4p-12f;
+constexpr float kPio2c = 0x1.4442d2p-24f;
+// 1/k! with alternating signs, binary32-rounded
+constexpr float kInv3 = -0x1.555556p-3f, kInv5 = 0x1.111112p-7f, kInv7 = -0x1.a01a02p-13f,
+                kInv9 = 0x1.71de3ap-19f;
+constexpr float kInv2 = -0.5f, kInv4 = 0x1.555556p-5f, kInv6 = -0x1.6c16c2p-10f, kInv8 = 0x1.a01a02p-16f,
+                kInv10 = -0x1.27e4fcp-22f;
+
+UBS_HD void sincos32(float x, float* s_out, float* c_out) {
+  const float j = rintf(x * kTwoOverPi);
+  const float r = ((x - j * kPio2a) - j * kPio2b) - j * kPio2c;
+  const float z = r * r;
+  const float s = r + r * (z * (kInv3 + z * (kInv5 + z * (kInv7 + z * kInv9))));
+  const float c = 1.0f + z * (kInv2 + z * (kInv4 + z * (kInv6 + z * (kInv8 + z * kInv10))));
+  const int q = ((int)j) & 3;
+  *s_out = q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
+  *c_out = q == 0 ? c : q == 1 ? -s : q == 2 ? -c : s;
 }
 
 UBS_HD float log32(float x) {

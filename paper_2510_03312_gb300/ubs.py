@@ -26,6 +26,7 @@ UBS_ROT_SKEW1 = 1
 UBS_ROT_SKEW2 = 2
 UBS_ROT_CAYLEY = 3
 UBS_ROT_CHOL = 4
+UBS_ROT_EXP = 5
 UBS_FLAG_TIGHT_CUT = 1
 UBS_FLAG_COUNT_PAIRS = 2
 UBS_FLAG_ACCUMULATE_GRADS = 4

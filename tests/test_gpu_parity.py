@@ -39,6 +39,7 @@ CASES = {
     "n3_skew2": lambda: _multi(3, 2500, 1, 160, 120, 16, mode=S.ROT_SKEW2),
     "n6_cayley_2views": lambda: _multi(6, 8000, 2, 150, 110, 17, mode=S.ROT_CAYLEY),
     "n7_chol_2views": lambda: _multi(7, 20000, 2, 150, 110, 18, mode=S.ROT_CHOL),
+    "n3_exp": lambda: _multi(3, 2500, 1, 160, 120, 19, mode=S.ROT_EXP),
     "n6_3views": lambda: _multi(6, 12000, 3, 176, 132, 13),
     "n7_3views": lambda: _multi(7, 30000, 3, 150, 110, 14),
     "n4_2views": lambda: _multi(4, 6000, 2, 130, 90, 15),
@@ -60,7 +61,7 @@ def test_forward_parity(case):
     print(f"{case}: max image error {worst:.2e}, flagged pixels {nflag}")
 
 
-@pytest.mark.parametrize("case", ["n3_ragged_2views", "n3_skew", "n3_skew2", "n6_cayley_2views", "n7_chol_2views",
+@pytest.mark.parametrize("case", ["n3_ragged_2views", "n3_skew", "n3_skew2", "n6_cayley_2views", "n7_chol_2views", "n3_exp",
                                   "n6_3views",
                                   "n7_3views", "n4_2views", "tile8", "tile32"])
 def test_backward_parity(case):
