@@ -354,11 +354,16 @@ class Oracle:
     def leaves(self, requires_grad=False):
         return [scene_leaves(s, requires_grad) for s in self.scenes]
 
-    def records(self, leaves):
+    def records(self, leaves, views=None):
         """Per view: float64 mean2d [P,2], conic [P,2,2], opacity [P],
-        beta_x [P], rgb [P,3], depth [P], cov2d [P,2,2], mean3 [P,3]."""
+        beta_x [P], rgb [P,3], depth [P], cov2d [P,2,2], mean3 [P,3].  With
+        ``views`` (indices), only those views' records are computed and the
+        others are None (a render restricted to their tiles needs no more)."""
         out = []
-        for v in self.views:
+        for vi, v in enumerate(self.views):
+            if views is not None and vi not in views:
+                out.append(None)
+                continue
             sc = self.scenes[v.scene_id]
             lv = leaves[v.scene_id]
             mu_c, Sc, oq, beta_x = condition(lv, sc.N, sc.rot_mode, v)
@@ -446,13 +451,16 @@ class Oracle:
         return composite_branches(r, alpha, beta, oq, rgb, cfg)
 
 
-def loss_grads(oracle, dL_dimage, tiles=None):
+def loss_grads(oracle, dL_dimage, tiles=None, views=None):
     """Gradient of sum(image * dL_dimage) with respect to every parameter
     plane block of every scene (autograd of the float64 forward), plus the
-    per-record gradients of the projected quantities."""
+    per-record gradients of the projected quantities.  ``views``: restrict the
+    records to these views (dL_dimage must vanish on the others)."""
     leaves = oracle.leaves(True)
-    recs = oracle.records(leaves)
+    recs = oracle.records(leaves, views=views)
     for R in recs:
+        if R is None:
+            continue
         for k in ("mean2d", "conic", "opacity", "beta_x", "rgb"):
             R[k].retain_grad()
     out = oracle.render(leaves=leaves, tiles=tiles, recs=recs)
@@ -466,6 +474,9 @@ def loss_grads(oracle, dL_dimage, tiles=None):
               for k, t in lv.items()} for lv in leaves]
     rec_grads = []
     for R in recs:
+        if R is None:
+            rec_grads.append(None)
+            continue
         rec_grads.append({k: (R[k].grad.numpy().copy() if R[k].grad is not None
                               else np.zeros(tuple(R[k].shape))) for k in
                           ("mean2d", "conic", "opacity", "beta_x", "rgb")})

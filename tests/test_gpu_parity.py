@@ -238,6 +238,31 @@ def test_full_size_static_sampled():
     check_grads(gpu, orc, ref, tiles=tiles)
 
 
+@pytest.mark.parametrize("make", [S.workload_view_dependent, S.workload_dynamic], ids=["n6_500k_16views",
+                                                                                      "n7_300k_8views"])
+def test_full_size_batched_sampled(make):
+    """The view-dependent (N=6, 500K primitives, 16 x 1280x720) and dynamic
+    (N=7, 300K primitives, 8 x 1352x1014) workloads in one launch with 16x16
+    tiles, the batched form the benchmark times: every record's integer
+    outputs and every sorted instance list bit-exact; records of the sampled
+    views, images, transmittance, last contributors and gradients on sampled
+    tiles (the densest three and six at random) against float64."""
+    wl = make()
+    orc = R64.Oracle(wl.scenes, wl.views, wl.cfg)
+    gpu = gpu_forward(wl.scenes, wl.views, wl.cfg)
+    check_bins(gpu, orc)
+    counts = np.diff(orc.bins["ranges"], axis=1)[:, 0]
+    order = np.argsort(-counts)
+    rng = np.random.default_rng(1)
+    nonempty = np.flatnonzero(counts)
+    tiles = sorted(set(order[:3].tolist()) | set(rng.choice(nonempty, 6, replace=False).tolist()))
+    views = sorted({orc.view_of_tile(g) for g in tiles})
+    recs = check_preprocess(gpu, orc, views=views)
+    worst, nflag, ref = check_images(gpu, orc, recs=recs, tiles=tiles)
+    print(f"{wl.name}: max image error {worst:.2e} on {len(tiles)} tiles of views {views}, flagged {nflag}")
+    check_grads(gpu, orc, ref, tiles=tiles, views=views)
+
+
 def test_empty_scenes():
     """A problem whose only scene has no primitives (no records at all)
     renders the background with nothing to sort; beside a non-empty scene,
