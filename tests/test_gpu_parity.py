@@ -238,12 +238,13 @@ def test_full_size_static_sampled():
     check_grads(gpu, orc, ref, tiles=tiles)
 
 
-@pytest.mark.parametrize("make", [S.workload_view_dependent, S.workload_dynamic], ids=["n6_500k_16views",
-                                                                                      "n7_300k_8views"])
+@pytest.mark.parametrize("make", [S.workload_view_dependent, S.workload_dynamic, S.workload_uneven_mix],
+                         ids=["n6_500k_16views", "n7_300k_8views", "mix_64jobs"])
 def test_full_size_batched_sampled(make):
-    """The view-dependent (N=6, 500K primitives, 16 x 1280x720) and dynamic
-    (N=7, 300K primitives, 8 x 1352x1014) workloads in one launch with 16x16
-    tiles, the batched form the benchmark times: every record's integer
+    """The view-dependent (N=6, 500K primitives, 16 x 1280x720), dynamic
+    (N=7, 300K primitives, 8 x 1352x1014) and uneven-mix (64 jobs over 8
+    scenes of 12K-1.9M primitives, 25M records) workloads in one launch with
+    16x16 tiles, the batched form the benchmark times: every record's integer
     outputs and every sorted instance list bit-exact; records of the sampled
     views, images, transmittance, last contributors and gradients on sampled
     tiles (the densest three and six at random) against float64."""
