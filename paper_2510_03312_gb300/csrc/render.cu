@@ -347,36 +347,30 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
 }
 
 // Transposed-butterfly reduction of g[0..9] over the warp: each exchange
-// step halves the values a lane keeps, so 12 shuffles sum all 10.  On return
-// lane l holds the warp total of value writer_of(l) (when that is >= 0).
+// step halves the values a lane keeps, so 12 shuffles sum all 10; the adds
+// of neighbouring slots run as packed float32 pairs.  On return lane l holds
+// the warp total of value writer_of(l) (when that is >= 0).
 __device__ __forceinline__ float warp_reduce10(const float (&g)[10], int lane) {
   const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  // bit 4: keep {0..4} (b4 = 0) or {5..9} (b4 = 1)
-  float p[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const float keep = b4 ? g[i + 5] : g[i];
-    const float send = b4 ? g[i] : g[i + 5];
-    p[i] = keep + __shfl_xor_sync(kFull, send, 16);
-  }
+  float2 k01 = b4 ? make_float2(g[5], g[6]) : make_float2(g[0], g[1]);
+  float2 k23 = b4 ? make_float2(g[7], g[8]) : make_float2(g[2], g[3]);
+  const float k4 = b4 ? g[9] : g[4];
+  const float e0 = b4 ? g[0] : g[5], e1 = b4 ? g[1] : g[6], e2 = b4 ? g[2] : g[7], e3 = b4 ? g[3] : g[8],
+              e4 = b4 ? g[4] : g[9];
+  const float2 p01 = add2(k01, make_float2(__shfl_xor_sync(kFull, e0, 16), __shfl_xor_sync(kFull, e1, 16)));
+  const float2 p23 = add2(k23, make_float2(__shfl_xor_sync(kFull, e2, 16), __shfl_xor_sync(kFull, e3, 16)));
+  const float p4 = k4 + __shfl_xor_sync(kFull, e4, 16);
   // bit 3: slots (p0|p3, p1|p4, p2)
-  float s[3];
-  {
-    const float k0 = b3 ? p[3] : p[0], e0 = b3 ? p[0] : p[3];
-    const float k1 = b3 ? p[4] : p[1], e1 = b3 ? p[1] : p[4];
-    s[0] = k0 + __shfl_xor_sync(kFull, e0, 8);
-    s[1] = k1 + __shfl_xor_sync(kFull, e1, 8);
-    s[2] = p[2] + __shfl_xor_sync(kFull, p[2], 8);
-  }
+  const float2 kk = b3 ? make_float2(p23.y, p4) : make_float2(p01.x, p01.y);
+  const float f0 = b3 ? p01.x : p23.y, f1 = b3 ? p01.y : p4;
+  const float2 s01 = add2(kk, make_float2(__shfl_xor_sync(kFull, f0, 8), __shfl_xor_sync(kFull, f1, 8)));
+  const float s2 = p23.x + __shfl_xor_sync(kFull, p23.x, 8);
   // bit 2: slots (s0|s1, s2)
-  float t[2];
-  {
-    const float k0 = b2 ? s[1] : s[0], e0 = b2 ? s[0] : s[1];
-    t[0] = k0 + __shfl_xor_sync(kFull, e0, 4);
-    t[1] = s[2] + __shfl_xor_sync(kFull, s[2], 4);
-  }
+  const float m0 = b2 ? s01.y : s01.x, h0 = b2 ? s01.x : s01.y;
+  const float2 t01 = add2(make_float2(m0, s2),
+                          make_float2(__shfl_xor_sync(kFull, h0, 4), __shfl_xor_sync(kFull, s2, 4)));
   // bit 1: slot t0|t1
-  const float k = b1 ? t[1] : t[0], e = b1 ? t[0] : t[1];
+  const float k = b1 ? t01.y : t01.x, e = b1 ? t01.x : t01.y;
   float u = k + __shfl_xor_sync(kFull, e, 2);
   // bit 0
   u += __shfl_xor_sync(kFull, u, 1);
