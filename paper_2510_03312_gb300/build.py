@@ -85,5 +85,34 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     return LIB
 
 
+def build_sanitized(out_dir: str) -> str:
+    """The same library with its host code under AddressSanitizer and
+    UndefinedBehaviorSanitizer (device code unchanged), for host-side tests of
+    the argument checks and layout arithmetic; built into out_dir.  Loading it
+    needs the sanitizer runtimes preloaded (LD_PRELOAD)."""
+    os.makedirs(out_dir, exist_ok=True)
+    cc = nvcc()
+    san = ["-Xcompiler", "-fPIC,-fsanitize=address,-fsanitize=undefined,-fno-omit-frame-pointer"]
+    common = [a for a in COMMON if a not in ("-Xcompiler", "-fPIC")]
+
+    def one(item):
+        name, extra = item
+        obj = os.path.join(out_dir, name.replace(".cu", ".o"))
+        r = subprocess.run([cc, *ARCH, *common, *san, *extra, "-c", os.path.join(CSRC, name), "-o", obj],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {name}:\n{r.stderr}")
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        objs = list(ex.map(one, UNITS.items()))
+    lib = os.path.join(out_dir, "libubs_sanitized.so")
+    r = subprocess.run([cc, *ARCH, "-shared", "-Xcompiler", "-fsanitize=address,-fsanitize=undefined", "-o", lib,
+                        *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    return lib
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
