@@ -219,6 +219,7 @@ size_t ubs_workspace_size(const ubs_problem* problem) {
 }
 
 ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_preprocess");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
@@ -276,6 +277,7 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
 }
 
 ubs_status ubs_bin_sort(const ubs_problem* pr, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_bin_sort");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
@@ -283,6 +285,7 @@ ubs_status ubs_bin_sort(const ubs_problem* pr, void* ws, size_t ws_bytes, cudaSt
 }
 
 ubs_status ubs_render_fwd(const ubs_problem* pr, void* ws, size_t ws_bytes, float* image, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_render_fwd");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
@@ -293,6 +296,7 @@ ubs_status ubs_render_fwd(const ubs_problem* pr, void* ws, size_t ws_bytes, floa
 
 ubs_status ubs_render_bwd_blend(const ubs_problem* pr, void* ws, size_t ws_bytes, const float* dL_dimage,
                                 cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_render_bwd_blend");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
@@ -303,6 +307,7 @@ ubs_status ubs_render_bwd_blend(const ubs_problem* pr, void* ws, size_t ws_bytes
 
 ubs_status ubs_render_bwd_params(const ubs_problem* pr, void* ws, size_t ws_bytes, const ubs_scene_grad* grads,
                                  cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_render_bwd_params");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
@@ -329,6 +334,7 @@ ubs_status ubs_render_bwd_params(const ubs_problem* pr, void* ws, size_t ws_byte
 
 ubs_status ubs_render_bwd(const ubs_problem* pr, void* ws, size_t ws_bytes, const float* dL_dimage,
                           const ubs_scene_grad* grads, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_render_bwd");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
@@ -344,6 +350,7 @@ ubs_status ubs_render_bwd(const ubs_problem* pr, void* ws, size_t ws_bytes, cons
 
 ubs_status ubs_read_status(const ubs_problem* pr, void* ws, size_t ws_bytes, ubs_device_status* out,
                            cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_read_status");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
@@ -361,6 +368,7 @@ ubs_status ubs_read_status(const ubs_problem* pr, void* ws, size_t ws_bytes, ubs
 
 ubs_status ubs_export(const ubs_problem* pr, void* ws, size_t ws_bytes, int32_t what, void* dst, size_t dst_bytes,
                       size_t* bytes_needed, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_export");
   Layout L;
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;

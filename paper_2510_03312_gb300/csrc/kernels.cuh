@@ -2,10 +2,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 
 namespace ubs {
+
+// An NVTX range named after a C-ABI entry point, open for the call (host
+// side; header-only NVTX3, a few nanoseconds when no profiler is attached),
+// so that profiler timelines group each call's launches.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Programmatic dependent launch (sm_90 and later): a kernel started with
 // launch_dependent may be scheduled while the previous kernel on the stream

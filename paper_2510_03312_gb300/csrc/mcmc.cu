@@ -240,6 +240,7 @@ extern "C" ubs_status ubs_mcmc_relocate(int32_t K, int64_t P, int32_t opacity_ro
                                         float* act, float* raw, float* m, float* v, const uint64_t* rand,
                                         int32_t* sources, int64_t* n_relocated, void* workspace,
                                         size_t workspace_bytes, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_mcmc_relocate");
   if (K < 1 || K > kMcMaxPlanes || P < 1 || P > (int64_t)0x7fffffff) return UBS_ERR_INVALID_ARG;
   if (opacity_row < 0 || opacity_row >= K || !(dead_threshold >= 0.0f && dead_threshold < 1.0f))
     return UBS_ERR_INVALID_ARG;

@@ -510,6 +510,7 @@ extern "C" size_t ubs_loss_workspace_size(int32_t n_views, const int32_t* widths
 extern "C" ubs_status ubs_image_loss(int32_t n_views, const int32_t* widths, const int32_t* heights,
                                      const float* image, const float* target, float lambda_ssim, float* dL_dimage,
                                      float* loss, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_image_loss");
   LossParams p;
   memset(&p, 0, sizeof(p));
   size_t need = 0;
@@ -545,6 +546,7 @@ extern "C" ubs_status ubs_image_loss(int32_t n_views, const int32_t* widths, con
 extern "C" ubs_status ubs_adam_step(int32_t K, int64_t P, const ubs_adam_plane* planes, const ubs_adam_config* cfg,
                                     float* raw, float* act_out, const float* grad, float* m, float* v,
                                     const float* noise, cudaStream_t stream) {
+  ubs::TraceRange trace_("ubs_adam_step");
   if (K < 1 || K > kAdamMaxPlanes || P < 0 || !planes || !cfg) return UBS_ERR_INVALID_ARG;
   if (P == 0) return UBS_OK;
   if (!raw || !act_out || !grad || !m || !v || raw == act_out) return UBS_ERR_INVALID_ARG;
