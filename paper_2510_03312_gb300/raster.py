@@ -16,6 +16,33 @@ from . import ubs as U
 from .scenes import PLANE_ORDER, RasterConfig, Scene, View, plane_rows
 
 
+def check_tensor(t, name: str, device: torch.device, dtype=torch.float32, shape=None, numel=None):
+    """Raises unless ``t`` is a contiguous tensor of ``dtype`` on ``device``
+    (type, and index when the device names one) with the given shape or
+    element count.  The C-ABI takes bare pointers and sizes it cannot check
+    against the allocation: a host pointer or a short buffer passed on would
+    reach the kernels, so every tensor is checked here before its pointer is."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor, not {type(t).__name__}")
+    if t.device.type != device.type or (device.index is not None and t.device.index != device.index):
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t
+
+
+def overlaps(a: torch.Tensor, b: torch.Tensor) -> bool:
+    """Whether the memory of two contiguous tensors overlaps."""
+    a0, b0 = a.data_ptr(), b.data_ptr()
+    return a0 < b0 + b.numel() * b.element_size() and b0 < a0 + a.numel() * a.element_size()
+
+
 def config_struct(cfg: RasterConfig) -> U.ubs_config:
     c = U.ubs_config()
     c.tile_w, c.tile_h = int(cfg.tile_w), int(cfg.tile_h)
@@ -98,6 +125,10 @@ class Rasterizer:
         self.views = list(views)
         self.cfg = cfg
         self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("the rasterizer runs on a CUDA device")
+        for s in self.scenes:
+            check_tensor(s.params, "scene params", self.device, shape=s.params.shape)
         self._scene_structs = (U.ubs_scene * len(self.scenes))(*[s.struct() for s in self.scenes])
         self._view_structs = (U.ubs_view * len(self.views))(*[view_struct(v) for v in self.views])
         self.problem = U.ubs_problem()
@@ -119,9 +150,10 @@ class Rasterizer:
             self.grads = [torch.empty_like(s.params) for s in self.scenes]
         else:
             self.grads = list(grads)
+            if len(self.grads) != len(self.scenes):
+                raise ValueError("one gradient tensor per scene is required")
             for g, s in zip(self.grads, self.scenes):
-                if g.shape != s.params.shape or g.dtype != torch.float32 or not g.is_contiguous():
-                    raise ValueError("each gradient tensor must be a contiguous float32 tensor shaped like params")
+                check_tensor(g, "gradient", self.device, shape=s.params.shape)
         self._grad_structs = (U.ubs_scene_grad * len(self.scenes))(
             *[s.grad_struct(g) for s, g in zip(self.scenes, self.grads)])
 
@@ -159,18 +191,22 @@ class Rasterizer:
         self._check(U.ubs_bin_sort(self.problem, self.ws_ptr, self.ws_bytes, self.stream()), "ubs_bin_sort")
 
     def render_fwd(self, image=None):
-        image = self.image if image is None else image
+        if image is None:
+            image = self.image
+        else:
+            check_tensor(image, "image", self.device, numel=3 * self.n_pix)
         self._check(U.ubs_render_fwd(self.problem, self.ws_ptr, self.ws_bytes, image.data_ptr(), self.stream()),
                     "ubs_render_fwd")
         return image
 
     def render_bwd(self, dL_dimage: torch.Tensor):
-        dL = dL_dimage.contiguous()
+        dL = check_tensor(dL_dimage.contiguous(), "dL_dimage", self.device, numel=3 * self.n_pix)
         self._check(U.ubs_render_bwd(self.problem, self.ws_ptr, self.ws_bytes, dL.data_ptr(), self._grad_structs,
                                      self.stream()), "ubs_render_bwd")
         return self.grads
 
     def render_bwd_blend(self, dL_dimage: torch.Tensor):
+        check_tensor(dL_dimage, "dL_dimage", self.device, numel=3 * self.n_pix)
         self._check(U.ubs_render_bwd_blend(self.problem, self.ws_ptr, self.ws_bytes, dL_dimage.data_ptr(),
                                            self.stream()), "ubs_render_bwd_blend")
 

@@ -18,6 +18,7 @@ import torch
 
 from . import scenes as S
 from . import ubs as U
+from .raster import check_tensor, overlaps
 
 LAMBDA_SSIM = 0.2  # not stated in the paper; the value of 3DGS, whose loss this extends
 
@@ -82,6 +83,8 @@ class ImageLoss:
         self.heights = [int(v.height) for v in views]
         self.lam = float(lambda_ssim)
         self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("ImageLoss runs on a CUDA device")
         n = U.ubs_loss_workspace_size(self.widths, self.heights)
         if n == 0:
             raise ValueError("invalid view sizes for ubs_image_loss")
@@ -89,9 +92,14 @@ class ImageLoss:
         self.ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
         self.ws_bytes = n
         self.loss = torch.zeros(1 + len(views), dtype=torch.float32, device=self.device)
+        self.numel = 3 * sum(w * h for w, h in zip(self.widths, self.heights))
 
     def __call__(self, image: torch.Tensor, target: torch.Tensor, dL: torch.Tensor) -> torch.Tensor:
         """Writes dL/dimage into ``dL``; returns the device tensor [total, per view]."""
+        for t, name in ((image, "image"), (target, "target"), (dL, "dL")):
+            check_tensor(t, name, self.device, numel=self.numel)
+        if overlaps(dL, image) or overlaps(dL, target):
+            raise ValueError("dL may not alias the image or the target")
         st = U.ubs_image_loss(self.widths, self.heights, image.data_ptr(), target.data_ptr(), self.lam,
                               dL.data_ptr(), self.loss.data_ptr(), self.ws_ptr, self.ws_bytes,
                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -108,7 +116,10 @@ class Adam:
     def __init__(self, scene, act: torch.Tensor, tc: TrainConfig | None = None):
         self.tc = tc or TrainConfig()
         self.table = plane_table(scene.N, scene.rot_mode, self.tc)
+        if act.dim() != 2:
+            raise ValueError("act must be a [K, P] parameter block")
         K, P = act.shape
+        check_tensor(act, "act", act.device, shape=(K, P))
         if K != len(self.table):
             raise ValueError("parameter block does not match the scene layout")
         self.K, self.P = K, P
@@ -125,6 +136,11 @@ class Adam:
     def step(self, grad: torch.Tensor, noise: torch.Tensor | None = None):
         """One step with dL/d(activated params) ``grad``; ``noise`` [3, P] is the
         drawn eps of the spatial noise (None: no noise)."""
+        if self.act.device.type != "cuda":
+            raise ValueError("the optimiser's tensors must be on a CUDA device to step")
+        check_tensor(grad, "grad", self.act.device, shape=(self.K, self.P))
+        if noise is not None:
+            check_tensor(noise, "noise", self.act.device, shape=(3, self.P))
         self.step_count += 1
         cfg = U.ubs_adam_config(self.tc.beta1, self.tc.beta2, self.tc.eps, self.step_count,
                                 self.tc.lambda_eps if noise is not None else 0.0)
@@ -199,6 +215,9 @@ class Relocator:
     def __call__(self, rand: torch.Tensor):
         """rand: [P] int64 tensor of random bits (read as uint64)."""
         o = self.opt
+        if o.act.device.type != "cuda":
+            raise ValueError("the optimiser's tensors must be on a CUDA device to relocate")
+        check_tensor(rand, "rand", o.act.device, dtype=torch.int64, shape=(o.P,))
         st = U.ubs_mcmc_relocate(o.K, o.P, self.opacity_row, self.threshold, o.act.data_ptr(), o.raw.data_ptr(),
                                  o.m.data_ptr(), o.v.data_ptr(), rand.data_ptr(), self.sources.data_ptr(),
                                  self.n_relocated.data_ptr(), self.ws_ptr, self.ws_bytes,

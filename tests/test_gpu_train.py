@@ -179,3 +179,32 @@ def test_training_resumes_from_a_checkpoint(dev, tmp_path):
     for name in ("raw", "act", "m", "v"):
         a, b = getattr(opt, name), getattr(opt2, name)
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-6), (name, float((a - b).abs().max()))
+
+
+def test_binding_rejects_bad_tensors_before_launching(dev):
+    """Host tensors, short buffers, other dtypes and an aliased gradient are
+    refused by the binding; the device keeps working afterwards."""
+    from paper_2510_03312_gb300 import raster
+    from paper_2510_03312_gb300 import train as TR
+    loss_fn = TR.ImageLoss([_V(16, 8)], device=dev)
+    img = torch.rand(3 * 16 * 8, device=dev)
+    tgt, dL = torch.rand_like(img), torch.empty_like(img)
+    for args in ((img.cpu(), tgt, dL), (img[:-1], tgt[:-1], dL[:-1]), (img, tgt, img), (img.double(), tgt, dL)):
+        with pytest.raises(ValueError):
+            loss_fn(*args)
+    wl = S.workload_static_small(P=500, size=32)
+    ds = raster.DeviceScene.from_scene(wl.scenes[0], device=dev)
+    r = raster.Rasterizer([ds], wl.views, wl.cfg, device=dev)
+    r.forward(check=True)
+    with pytest.raises(ValueError):
+        r.render_fwd(torch.empty(10, device=dev))
+    with pytest.raises(ValueError):
+        r.render_bwd_blend(torch.empty(3 * r.n_pix))
+    with pytest.raises(ValueError):
+        r.render_bwd(torch.empty(3 * r.n_pix, device=dev, dtype=torch.float64))
+    opt = TR.Adam(wl.scenes[0], ds.params)
+    with pytest.raises(ValueError):
+        opt.step(torch.zeros(opt.K, opt.P + 1, device=dev))
+    out = loss_fn(img, tgt, dL)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
