@@ -130,6 +130,7 @@ class Rasterizer:
         for s in self.scenes:
             check_tensor(s.params, "scene params", self.device, shape=s.params.shape)
         self._scene_structs = (U.ubs_scene * len(self.scenes))(*[s.struct() for s in self.scenes])
+        self._param_ptrs = [s.params.data_ptr() for s in self.scenes]
         self._view_structs = (U.ubs_view * len(self.views))(*[view_struct(v) for v in self.views])
         self.problem = U.ubs_problem()
         self.problem.scenes = self._scene_structs
@@ -185,6 +186,10 @@ class Rasterizer:
 
     # -- steps
     def preprocess(self):
+        # the problem holds the parameter pointers taken at construction
+        if any(s.params.data_ptr() != p for s, p in zip(self.scenes, self._param_ptrs)):
+            raise ValueError("a scene's params tensor was replaced after the rasterizer was built "
+                             "(update it in place, or build a new Rasterizer)")
         self._check(U.ubs_preprocess(self.problem, self.ws_ptr, self.ws_bytes, self.stream()), "ubs_preprocess")
 
     def bin_sort(self):

@@ -208,3 +208,6 @@ def test_binding_rejects_bad_tensors_before_launching(dev):
     out = loss_fn(img, tgt, dL)
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
+    ds.params = ds.params.clone()  # the problem still holds the old pointers
+    with pytest.raises(ValueError, match="replaced"):
+        r.preprocess()
