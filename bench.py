@@ -821,7 +821,7 @@ def main():
     # the CPU baseline runs first, in this process before any CUDA work
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.primitives, n_tiles=400)
+        cpu = oracle_sample(args.primitives, n_tiles=1200)
     out = bench_ours(args, rank, world, local)
     if rank == 0:
         out["cpu_baseline"] = cpu
