@@ -65,3 +65,26 @@ def test_each_rank_renders_its_own_camera_of_the_same_scene():
     v0, v1 = w0.views[0], w1.views[0]
     assert (v0.width, v0.height) == (v1.width, v1.height) == (1600, 1060)
     assert not np.allclose(v0.R, v1.R)  # another camera on the same radius-8 sphere
+
+
+def test_reference_arm_prints_one_line_on_rank_zero_only():
+    """``bench.py --impl reference`` times the oracle on the host cores and
+    prints the bench line with ``impl: reference``; under torchrun the other
+    ranks return without work."""
+    import json
+    import subprocess
+    import sys
+
+    assert bench.bench_reference(None, 1, 2) is None
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1",
+                        "--primitives", "20000"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["metric"] == bench.METRIC and out["unit"] == "MP/s"
+    assert out["value"] > 0 and out["steps"] == 1 and out["warmup"] == 1 and out["higher_is_better"] is True
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"] == {"value": out["value"], "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert out["config"]["workload"] == "static_n3_1m_1600x1060"
