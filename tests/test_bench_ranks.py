@@ -88,3 +88,21 @@ def test_reference_arm_prints_one_line_on_rank_zero_only():
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
     assert out["e2e"] == {"value": out["value"], "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert out["config"]["workload"] == "static_n3_1m_1600x1060"
+
+
+def test_our_arm_fails_loudly_without_a_gpu():
+    """No CPU fallback: without a CUDA device the bench exits non-zero and
+    prints no result line."""
+    import subprocess
+    import sys
+
+    import pytest
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--no-cpu-baseline", "--no-batched", "--steps", "1", "--warmup", "3"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0
+    assert '"value"' not in r.stdout
