@@ -1,7 +1,8 @@
 """The host side of the C-ABI (argument checks, workspace layout and sizes)
 under AddressSanitizer and UndefinedBehaviorSanitizer: the library is built
-with both on its host code and the host ABI tests run against it in a child
-process; any sanitizer report fails the test.  No GPU is used."""
+with both on its host code and the host ABI tests (and the layout property
+tests) run against it in a child process; any sanitizer report fails the
+test.  No GPU is used."""
 import os
 import shutil
 import subprocess
@@ -32,7 +33,8 @@ def test_host_abi_under_sanitizers(tmp_path):
         f"sys.path.insert(0, {ROOT!r}); sys.path.insert(0, {os.path.join(ROOT, 'tests')!r})\n"
         "from paper_2510_03312_gb300 import ubs as U\n"
         f"U.load({lib!r})\n"
-        f"sys.exit(pytest.main(['-q', '-p', 'no:cacheprovider', {os.path.join(ROOT, 'tests', 'test_abi_host.py')!r}]))\n"
+        f"sys.exit(pytest.main(['-q', '-p', 'no:cacheprovider', {os.path.join(ROOT, 'tests', 'test_abi_host.py')!r}, "
+        f"{os.path.join(ROOT, 'tests', 'test_abi_layout_props.py')!r}]))\n"
     )
     env = dict(os.environ, LD_PRELOAD=f"{asan} {ubsan}", ASAN_OPTIONS="detect_leaks=0:halt_on_error=1",
                UBSAN_OPTIONS="halt_on_error=1:print_stacktrace=1")
