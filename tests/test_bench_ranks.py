@@ -106,3 +106,14 @@ def test_our_arm_fails_loudly_without_a_gpu():
                        cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0
     assert '"value"' not in r.stdout
+
+
+def test_traffic_figures_come_from_the_committed_profiles(monkeypatch):
+    """The roofline's DRAM traffic is read from the committed ncu summaries,
+    and only while the kernel's source is the one that was captured."""
+    for kernel in ("render_bwd_blend", "render_fwd"):
+        b = bench.traffic_record(kernel)
+        assert b is None or b > 0
+    assert bench.traffic_record("no_such_kernel") is None
+    monkeypatch.setattr(bench, "source_sha", lambda path: "0" * 16)
+    assert bench.traffic_record("render_bwd_blend") is None
