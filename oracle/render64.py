@@ -39,8 +39,13 @@ second-order rotations against SciPy (rotation map, rotation vector, expm),
 closed-form footprints, brute-force
 depth-sorted compositing, transmittance invariants, the static reduction of
 N=6/7 to N=3, Gaussian conditioning at beta~ = 1 against the precision-block
-identity, the Gaussian limit of the Beta kernel, the paper's printed beta
-values, and central finite differences for the gradients.
+identity, the Beta-modulated conditioning at 0 < beta~ < 1 (scalar-query
+closed forms, per-dimension sums where Sigma_q is diagonal, the regression
+matrix from the precision blocks, the vanishing-beta limits), invariance of
+the image under a rigid motion of scene and camera, the view direction of a
+camera placed at a known centre, the Gaussian limit of the Beta kernel, the
+paper's printed beta values, and central finite differences for the
+gradients.
 """
 from __future__ import annotations
 
