@@ -84,6 +84,13 @@ def job_throughput(world, steps, units_per_rank_step, total_ms):
     return world * steps * units_per_rank_step / (total_ms / 1e3)
 
 
+def config_of(wl, world):
+    """The workload-identifying keys of the bench line, shared by both arms."""
+    v = wl.views[0]
+    return {"workload": wl.name, "primitives": wl.scenes[0].P, "views": len(wl.views), "width": v.width,
+            "height": v.height, "tile": f"{wl.cfg.tile_w}x{wl.cfg.tile_h}", "parallelism": f"replicas x{world}"}
+
+
 def workload(rank, P):
     from paper_2510_03312_gb300 import scenes as S
 
@@ -251,7 +258,7 @@ def step_rooflines(stage_ms, names, params_bytes, R, instances, NT, pairs, pk, n
         else:
             tr = max(w[0] / fp32, w[1] / mufu)
             out[n] = {"bound": "alu", "fp32_ops": int(w[0]), "mufu_ops": int(w[1]),
-                      "achieved": round(w[0] / t / 1e12, 3), "peak": round(fp32 / 1e12, 2), "unit": "TFLOP/s",
+                      "achieved": round(w[0] / t / 1e12, 3), "peak": round(fp32 / 1e12, 2), "unit": "T lane-op/s",
                       "frac": round(tr / t, 4)}
         out[n]["ms"] = round(float(ms), 4)
         t_roof += tr
@@ -285,11 +292,13 @@ def bench_ours(args, rank, world, local):
     target = r.pack(S.l1_target(1, wl.views))
     dL = (torch.sign(img - target) / img.numel()).contiguous()
     torch.cuda.synchronize()
-    # pair count (diagnostic kernel variant, outside the timed region)
-    r.problem.cfg.flags |= 2
-    r.render_fwd()
-    pairs = int(r.export(9).to(torch.int64).sum().item())
-    r.problem.cfg.flags &= ~2
+    # pair counts (diagnostic kernel variant, outside the timed region): pairs
+    # with r < 1 met before each pixel terminates (tile-free), and the
+    # entries the forward's warps evaluate
+    cnt = raster.count_pairs([ds], wl.views, wl.cfg, device=dev)
+    pairs = int(cnt["pairs"].sum().item())
+    visited = int(cnt["visited"].sum().item())
+    del cnt
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -354,9 +363,9 @@ def bench_ours(args, rank, world, local):
         peak = alu_peak_tops(n_sm, pk.get("sm_max_mhz", 2070.0))
         kern = "render_bwd_blend" if names[dom] == "render_bwd_blend" else "render_fwd"
         roof = {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic_record(kern),
+                "unit": "T lane-op/s", "frac": round(ach / peak, 4), "traffic": traffic_record(kern),
                 "work": f"{ops_per_pair[names[dom]]} FP32 lane-ops per pair x {pairs} pairs",
-                "peak_source": f"152 SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
                                f"(clock of {pk_src} peaks file)"}
     else:
         nbytes = {"preprocess": 60 * sc.P + 44 * sc.P}.get(names[dom])
@@ -394,12 +403,13 @@ def bench_ours(args, rank, world, local):
         "metric": METRIC, "value": round(value, 2), "unit": "MP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "primitives": sc.P, "views": len(wl.views),
-                   "width": wl.views[0].width, "height": wl.views[0].height,
-                   "tile": f"{wl.cfg.tile_w}x{wl.cfg.tile_h}", "parallelism": f"replicas x{world}",
-                   "l2": "flushed (2x L2 buffer written) between timed steps",
-                   "instances": int(st.instances), "visible_records": int(st.visible_records),
-                   "pairs": pairs},
+        "config": config_of(wl, world),
+        "l2": "flushed (2x L2 buffer written) between timed steps",
+        "counts": {"instances": int(st.instances), "visible_records": int(st.visible_records),
+                   "pairs": pairs, "visited_pairs": visited,
+                   "pairs_definition": "pixels x records with r < 1 met before the pixel terminates, "
+                                       "tile-free (lists without the tight cut); visited = entries the "
+                                       "forward's warps evaluate x pixels of the warp"},
         "views_per_sec": round(job_throughput(world, args.steps, 1, total_ms), 2),
         "stage_ms": {n: round(float(m), 4) for n, m in zip(names, stage_mean)},
         "roofline": roof,
@@ -645,13 +655,14 @@ def batched_rooflines(ds, wl, dev, pk, n_sm, steps, warmup):
 
     from paper_2510_03312_gb300 import raster
 
+    cnt = raster.count_pairs(ds, wl.views, wl.cfg, device=dev)
+    pairs = int(cnt["pairs"].sum().item())
+    visited = int(cnt["visited"].sum().item())
+    del cnt
+    torch.cuda.empty_cache()
     r = raster.Rasterizer(ds, wl.views, wl.cfg, device=dev)
     img = r.forward(check=True)
     st = r.status()
-    r.problem.cfg.flags |= 2
-    r.render_fwd()
-    pairs = int(r.export(9).to(torch.int64).sum().item())
-    r.problem.cfg.flags &= ~2
     dL = torch.full_like(img, 1e-6)
     names = ["preprocess", "bin_sort", "render_fwd", "render_bwd_blend", "render_bwd_params"]
     stream = torch.cuda.current_stream()
@@ -673,7 +684,7 @@ def batched_rooflines(ds, wl, dev, pk, n_sm, steps, warmup):
     steps_roof, path = step_rooflines(stage, names, batch_pb, R, int(st.instances), r.n_tiles(), pairs, pk, n_sm)
     del r
     torch.cuda.empty_cache()
-    return steps_roof, path, batch_pb, view_pb, pairs
+    return steps_roof, path, batch_pb, view_pb, pairs, visited
 
 
 def bench_batched(dev, pk, n_sm, steps=5, warmup=2):
@@ -732,10 +743,12 @@ def bench_batched(dev, pk, n_sm, steps=5, warmup=2):
         out["speedup_batched"] = round(out["per_view"]["ms_per_step"] / out["batched"]["ms_per_step"], 3)
         del b, dls, g
         torch.cuda.empty_cache()
-        steps_roof, path, batch_pb, view_pb, pairs = batched_rooflines(ds, wl, dev, pk, n_sm, steps, warmup)
+        steps_roof, path, batch_pb, view_pb, pairs, visited = batched_rooflines(ds, wl, dev, pk, n_sm, steps,
+                                                                                warmup)
         t_roof = path["t_roof_ms"]
         t_roof_pv = t_roof + 3 * (view_pb - batch_pb) / (pk["hbm_gbs"] * 1e9) * 1e3
         out["pairs"] = pairs
+        out["visited_pairs"] = visited
         out["roofline_steps"] = steps_roof
         out["roofline_path"] = path
         for form, tr in (("per_view", t_roof_pv), ("batched_one_launch", t_roof), ("batched", t_roof)):
@@ -795,16 +808,20 @@ def bench_reference(args, rank, world):
     steps = []
     for i in range(args.warmup):
         oracle_sample(args.primitives, n_tiles=4, seed=100 + i)
+    t0 = time.perf_counter()
     for i in range(args.steps):
         steps.append(oracle_sample(args.primitives, n_tiles=24, seed=i))
+    timed_s = time.perf_counter() - t0
     v = float(np.mean([s["value"] for s in steps]))
     s0 = steps[0]
-    wl_name = workload(0, 8).name
+    # every step is a bounded sample; its measured seconds are the timed
+    # region, the whole-view seconds it stands for are extrapolated
     return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "MP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * s0["extrapolated_s_per_step"], 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * timed_s / args.steps, 1),
+            "extrapolated_ms_per_full_step": round(1e3 * float(np.mean([s["extrapolated_s_per_step"]
+                                                                          for s in steps])), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "static_n3_1m_1600x1060", "primitives": args.primitives,
-                                            "views": 1, "width": 1600, "height": 1060},
+            "data": "synthetic", "config": config_of(workload(0, args.primitives), world),
             "cpu_baseline": {"value": round(v, 5), "unit": "MP/s", "cores": s0["cores"], "kind": "oracle",
                              "sample": s0["sample"]},
             "e2e": {"value": round(v, 5), "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

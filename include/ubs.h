@@ -61,7 +61,8 @@ typedef enum {
   UBS_ERR_ALIGNMENT = 2,   /* a pointer or the workspace is misaligned */
   UBS_ERR_CAPACITY = 3,    /* more tile instances than instance_capacity */
   UBS_ERR_CUDA = 4,        /* a CUDA launch or copy failed */
-  UBS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  UBS_ERR_TIMEOUT = 5,     /* reserved: no kernel of this library waits on another block,
+                              so no call returns it; the value is kept so that codes stay stable */
   UBS_ERR_INTERNAL = 6,
   UBS_ERR_WORKSPACE = 7    /* workspace smaller than ubs_workspace_size */
 } ubs_status;
@@ -82,7 +83,8 @@ enum { UBS_ROT_QUAT = 0, UBS_ROT_SKEW1 = 1, UBS_ROT_SKEW2 = 2, UBS_ROT_CAYLEY = 
 enum {
   UBS_FLAG_TIGHT_CUT = 1, /* cut each footprint at r_cut = 1-(a_min/o(q))^(1/beta_x) */
   UBS_FLAG_COUNT_PAIRS = 2, /* diagnostic: ubs_render_fwd runs a variant that also counts,
-                               per pixel, the visited pairs with r < 1 (ubs_export 9) */
+                               per pixel, the pairs with r < 1 and the evaluated entries
+                               (ubs_export 9 and 10) */
   UBS_FLAG_ACCUMULATE_GRADS = 4 /* ubs_render_bwd / ubs_render_bwd_params ADD the parameter
                                    gradients to the ubs_scene_grad buffers instead of
                                    overwriting them: a scene rendered by several problems
@@ -243,9 +245,14 @@ ubs_status ubs_read_status(const ubs_problem* problem, void* workspace, size_t w
  * [instances] u32, 5 = tile starts [tiles + 1] u32, 6 = final T [pixels]
  * f32, 7 = last contributor [pixels] u32, 8 = per-record screen gradients
  * [R] x 12 f32 (3 and 8 are defined for the visible records, those with
- * tiles_touched > 0), 9 = visited pairs with r < 1 [pixels] u32 (written by the
- * UBS_FLAG_COUNT_PAIRS variant of ubs_render_fwd).  `dst` is device memory of at least `dst_bytes`; returns the
- * bytes needed in *bytes_needed. */
+ * tiles_touched > 0); written only by the UBS_FLAG_COUNT_PAIRS variant of
+ * ubs_render_fwd: 9 = per pixel, the pairs with r < 1 on its tile's list
+ * visited before the pixel terminated [pixels] u32 (without
+ * UBS_FLAG_TIGHT_CUT every record with r < 1 at the pixel is on that list,
+ * so this is the tile-free count), 10 = per pixel, the list entries its
+ * warp evaluated (those passing the blend's support cull, walked before the
+ * warp's 64 pixels were all done) [pixels] u32.  `dst` is device memory of
+ * at least `dst_bytes`; returns the bytes needed in *bytes_needed. */
 ubs_status ubs_export(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
                       int32_t what, void* dst, size_t dst_bytes, size_t* bytes_needed,
                       cudaStream_t stream);
@@ -354,11 +361,21 @@ ubs_status ubs_mcmc_relocate(int32_t K, int64_t P, int32_t opacity_row, float de
  *   call's contents (each step clears what must start at zero); calls whose
  *   work overlaps on the GPU race on it.
  * - As with ubs_bin_sort, if problem->instance_capacity is too small the
- *   image is left unwritten; size the capacity for the scene.
+ *   image is left unwritten (its previous contents stay) and the device
+ *   status becomes UBS_ERR_CAPACITY with the required instance count; read
+ *   it with ubs_read_status_static.
  * - Calls no cudaMalloc, cudaFree or allocating library routine.  The array
  *   stays allocated on every GPU that loaded this part of the library until
  *   the process exits. */
 ubs_status ubs_render_fwd_static(const ubs_problem* problem, float* image, cudaStream_t stream);
+
+/* The device status of the last ubs_render_fwd_static on the current
+ * device, as ubs_read_status gives it for a caller workspace: synchronises
+ * `stream` and copies the status header of the fixed array into *out (host).
+ * `problem` must be the problem of that call (its layout locates the
+ * header); returns UBS_ERR_WORKSPACE when it exceeds the array.  Allocates
+ * nothing. */
+ubs_status ubs_read_status_static(const ubs_problem* problem, ubs_device_status* out, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -240,15 +240,26 @@ def alpha_band(r, beta):
 
 
 T_BAND = 1e-4
+R_BAND = 4e-6   # |r - 1| within which float32 may decide r < 1 either way
 
 
-def _composite_block(px, py, mu2, conic, oq, beta, rgb, cfg):
+def _composite_block(px, py, mu2, conic, oq, beta, rgb, cfg, extra=None):
     """Vectorised compositing of M pixels over one front-to-back list of K
     records (tensors gathered in list order).  Returns colour [M,3], final T
-    [M], last-contributor count [M] and a per-pixel ambiguity flag."""
+    [M], last-contributor count [M] and a per-pixel ambiguity flag.  With a
+    dict ``extra``, also the pair count of each pixel, the number of list
+    entries with r < 1 visited before the pixel terminates (the stopping
+    entry included), as the interval [pairs_lo, pairs_hi] that float32
+    evaluation of r admits: r < 1 is decided on the float32 conic
+    (``extra["count_conic"]``, [K, 3] a, b, c, when given) and is ambiguous
+    within R_BAND plus 1e-6 of the magnitude of r's three terms (the float32
+    rounding of terms that cancel)."""
     M, K = px.shape[0], mu2.shape[0]
     bg = torch.tensor(cfg.bg, dtype=D)
     if K == 0:
+        if extra is not None:
+            extra["pairs_lo"] = torch.zeros(M, dtype=torch.long)
+            extra["pairs_hi"] = torch.zeros(M, dtype=torch.long)
         return (bg.expand(M, 3).clone(), torch.ones(M, dtype=D),
                 torch.zeros(M, dtype=torch.long), torch.zeros(M, dtype=torch.bool))
     dx = px[:, None] - mu2[None, :, 0]
@@ -282,6 +293,19 @@ def _composite_block(px, py, mu2, conic, oq, beta, rgb, cfg):
         reach = (ar <= first[:, None]).numpy()
         ft = used.numpy() & reach & (np.abs(Tp - tmin) <= T_BAND * tmin)
         flag = torch.from_numpy((fa | fr | ft).any(1))
+        if extra is not None:
+            dxd, dyd = dx.detach(), dy.detach()
+            cc = extra.get("count_conic")
+            if cc is None:
+                ca, cb, ccc = a.detach(), b.detach(), c.detach()
+            else:
+                ca, cb, ccc = cc[None, :, 0], cc[None, :, 1], cc[None, :, 2]
+            rc = ca * dxd * dxd + 2.0 * cb * dxd * dyd + ccc * dyd * dyd
+            mag = (ca * dxd * dxd).abs() + (2.0 * cb * dxd * dyd).abs() + (ccc * dyd * dyd).abs()
+            band = R_BAND + 1e-6 * mag
+            vis = ar <= first[:, None]
+            extra["pairs_lo"] = ((rc < 1.0 - band) & vis).sum(1)
+            extra["pairs_hi"] = ((rc < 1.0 + band) & vis).sum(1)
     w = torch.where(incl, alpha * Tb, torch.zeros_like(alpha))
     Text = torch.cat([Tb, Tc[:, -1:]], 1)
     Tfin = torch.gather(Text, 1, first[:, None])[:, 0]
@@ -386,13 +410,15 @@ class Oracle:
             leaves = self.leaves(False)
         if recs is None:
             recs = self.records(leaves)
-        images, Ts, lasts, flags = [], [], [], []
+        images, Ts, lasts, flags, plo, phi = [], [], [], [], [], []
         for vi, v in enumerate(self.views):
             H, W = v.height, v.width
             images.append(torch.full((3, H, W), float("nan"), dtype=D))
             Ts.append(torch.full((H, W), float("nan"), dtype=D))
             lasts.append(torch.full((H, W), -1, dtype=torch.long))
             flags.append(torch.zeros((H, W), dtype=torch.bool))
+            plo.append(torch.full((H, W), -1, dtype=torch.long))
+            phi.append(torch.full((H, W), -1, dtype=torch.long))
         if tiles is None:
             tiles = range(int(self.tile_off[-1]))
         ranges = self.bins["ranges"]
@@ -421,15 +447,19 @@ class Oracle:
                 s, e = ranges[g]
                 lst = torch.from_numpy(rec_sorted[s:e] - self.rec_off[vi])
             R = recs[vi]
+            c32 = self.pre32[vi]["conic"]
+            ext = {"count_conic": torch.from_numpy(c32.T[lst.numpy()].astype(np.float64))}
             col, T, last, flag = _composite_block(px, py, R["mean2d"][lst], R["conic"][lst],
                                                   R["opacity"][lst], R["beta_x"][lst],
-                                                  R["rgb"][lst], cfg)
+                                                  R["rgb"][lst], cfg, ext)
             hh, ww = y1 - y0, x1 - x0
+            plo[vi][y0:y1, x0:x1] = ext["pairs_lo"].reshape(hh, ww)
+            phi[vi][y0:y1, x0:x1] = ext["pairs_hi"].reshape(hh, ww)
             images[vi][:, y0:y1, x0:x1] = col.T.reshape(3, hh, ww)
             Ts[vi][y0:y1, x0:x1] = T.reshape(hh, ww)
             lasts[vi][y0:y1, x0:x1] = last.reshape(hh, ww)
             flags[vi][y0:y1, x0:x1] = flag.reshape(hh, ww)
-        return {"image": images, "T": Ts, "last": lasts, "flag": flags}
+        return {"image": images, "T": Ts, "last": lasts, "flag": flags, "pairs_lo": plo, "pairs_hi": phi}
 
     def admissible(self, vi, x, y, recs=None, tile_free=False):
         """All admissible (colour, T, last) results of pixel (x, y) of view vi."""

@@ -128,7 +128,7 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.order_count = take(2 * 132 * 4);  // zeroed with the per-pass counts
   L.Tfin = take((size_t)L.NPIX * 4);
   L.last = take((size_t)L.NPIX * 4);
-  L.pairs = take((size_t)L.NPIX * 4);
+  L.pairs = take((size_t)L.NPIX * 8);  // pairs with r < 1, then visited entries
   L.total = o;
   return UBS_OK;
 }
@@ -384,6 +384,7 @@ ubs_status ubs_export(const ubs_problem* pr, void* ws, size_t ws_bytes, int32_t 
     case 7: off = L.last; n = (size_t)L.NPIX * 4; break;
     case 8: off = L.g2d; n = (size_t)L.R * kGradFloats * 4; break;
     case 9: off = L.pairs; n = (size_t)L.NPIX * 4; break;
+    case 10: off = L.pairs + (size_t)L.NPIX * 4; n = (size_t)L.NPIX * 4; break;
     default: return UBS_ERR_INVALID_ARG;
   }
   if (bytes_needed) *bytes_needed = n;

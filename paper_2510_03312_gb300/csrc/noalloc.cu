@@ -17,7 +17,14 @@
 // stream capture begins.  All calls on a device share the one array and it
 // keeps the previous call's contents; the steps reset what must start at
 // zero themselves.  Two calls whose work overlaps on the GPU (different
-// streams, or different host threads) race on the array.
+// streams, or different host threads) race on the array.  The cached address
+// is never looked up again, so a device reset (cudaDeviceReset) after the
+// first call on that device is not supported.
+//
+// What the device-side steps report (an instance capacity too small for the
+// scene, with the count it needs) sits in the array's status header, which
+// ubs_read_status_static copies out, as ubs_read_status does for a
+// caller-owned workspace.
 #include <atomic>
 
 #include "ubs.h"
@@ -70,4 +77,16 @@ extern "C" ubs_status ubs_render_fwd_static(const ubs_problem* problem, float* i
   st = ubs_bin_sort(problem, ws, kStaticScratchBytes, stream);
   if (st != UBS_OK) return st;
   return ubs_render_fwd(problem, ws, kStaticScratchBytes, image, stream);
+}
+
+extern "C" ubs_status ubs_read_status_static(const ubs_problem* problem, ubs_device_status* out,
+                                             cudaStream_t stream) {
+  if (!problem || !out) return UBS_ERR_INVALID_ARG;
+  const size_t need = ubs_workspace_size(problem);
+  if (need == 0) return UBS_ERR_INVALID_ARG;
+  if (need > kStaticScratchBytes) return UBS_ERR_WORKSPACE;
+  ubs_status st = UBS_OK;
+  void* ws = scratch_for_current_device(&st);
+  if (!ws) return st;
+  return ubs_read_status(problem, ws, kStaticScratchBytes, out, stream);
 }

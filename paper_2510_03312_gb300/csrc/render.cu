@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
     render_fwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
                       const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
                       float* __restrict__ image, float* __restrict__ Tfin, uint32_t* __restrict__ lastc,
-                      const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs,
+                      const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs, uint32_t* __restrict__ visited,
                       const uint32_t* __restrict__ tile_order, uint32_t n_tiles, uint32_t cap) {
   wait_prior_grid();
   constexpr int NT = TW * TH / 2;           // threads: two pixels each
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
   const float2 one = make_float2(1.0f, 1.0f), neg1 = make_float2(-1.0f, -1.0f);
   uint8_t* list = s_list[threadIdx.x >> 5];
   float2 T = one, C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0;
-  uint32_t last0 = 0, last1 = 0, np0 = 0, np1 = 0;
+  uint32_t last0 = 0, last1 = 0, np0 = 0, np1 = 0, nv = 0;
   bool done0 = !in0, done1 = !in1;
   for (uint32_t base = start; base < end; base += BS) {
     if (__syncthreads_count(done0 && done1) == NT) break;
@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
     }
     __syncthreads();
     const int n = (int)min((uint32_t)BS, end - base);
-    // the counting variant visits every pair with r < 1
+    // the counting variant walks every entry, to count every pair with r < 1,
+    // and also counts the entries the cull would have kept (visited)
     const int cnt = warp_cull_list2(s_bb, s_A, s_B, s_C, s_rc, n, COUNT, wx0, wx1, wy0, wy1, list);
     const uint32_t rel = base - start;
     // one entry for both pixels; branch-free: a pair that is skipped (or
@@ -297,6 +298,9 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
       if constexpr (COUNT) {
         np0 += (!done0 && r.x < 1.0f);
         np1 += (!done1 && r.y < 1.0f);
+        const float4 A = s_A[j], Bc = s_B[j];
+        nv += box_hits(s_bb[j], wx0, wx1, wy0, wy1) &&
+              ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), s_C[j].x, s_rc[j], wx0, wx1, wy0, wy1);
       }
       const bool u0 = !done0 && r.x < 1.0f && al0 >= cfg.amin;
       const bool u1 = !done1 && r.y < 1.0f && al1 >= cfg.amin;
@@ -333,7 +337,10 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
     img[2 * plane + pix] = fmaf(T.x, cfg.bg[2], C2.x);
     Tfin[v.pix_off + pix] = T.x;
     lastc[v.pix_off + pix] = last0;
-    if constexpr (COUNT) pairs[v.pix_off + pix] = np0;
+    if constexpr (COUNT) {
+      pairs[v.pix_off + pix] = np0;
+      visited[v.pix_off + pix] = nv;
+    }
   }
   if (in1) {
     const size_t pix = (size_t)y1 * v.W + x;
@@ -342,7 +349,10 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
     img[2 * plane + pix] = fmaf(T.y, cfg.bg[2], C2.y);
     Tfin[v.pix_off + pix] = T.y;
     lastc[v.pix_off + pix] = last1;
-    if constexpr (COUNT) pairs[v.pix_off + pix] = np1;
+    if constexpr (COUNT) {
+      pairs[v.pix_off + pix] = np1;
+      visited[v.pix_off + pix] = nv;
+    }
   }
 }
 
@@ -587,13 +597,14 @@ cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cu
   const uint32_t R = L.R > 0 ? L.R : 1;
   constexpr int NT = TW * TH;
   const uint32_t* order = order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr;
-  if (cfg.flags & 2)  // diagnostic variant: also count visited pairs with r < 1 per pixel
+  if (cfg.flags & 2)  // diagnostic variant: also count, per pixel, the pairs with r < 1 and the visited entries
     launch_dependent(render_fwd_kernel<TW, TH, true>, dim3(L.NT), dim3(NT / 2), 0, st, views, L.V, cfg, tstart,
-                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs), order,
-                     L.NT, L.cap);
+                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs),
+                     (uint32_t*)(ws + L.pairs) + L.NPIX, order, L.NT, L.cap);
   else
     launch_dependent(render_fwd_kernel<TW, TH, false>, dim3(L.NT), dim3(NT / 2), 0, st, views, L.V, cfg, tstart,
-                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, nullptr, order, L.NT, L.cap);
+                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, nullptr, nullptr, order, L.NT,
+                     L.cap);
   return cudaGetLastError();
 }
 

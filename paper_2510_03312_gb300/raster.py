@@ -275,6 +275,31 @@ class Rasterizer:
         return out.view(dtype)
 
 
+def count_pairs(scenes, views, cfg: RasterConfig, device="cuda"):
+    """Per-pixel diagnostic counts of the forward blend, from its counting
+    variant (UBS_FLAG_COUNT_PAIRS), as int64 tensors over the packed pixels:
+
+    * ``pairs``: (pixel, record) pairs with r < 1 visited before the pixel
+      terminates, counted on lists built without the tight cut, so that
+      every record whose support ellipse holds the pixel is on its tile's
+      list: the tile-independent pair count;
+    * ``visited``: the entries each pixel's warp evaluated in the forward
+      with the configuration's own lists (those its support cull keeps,
+      walked until the warp's pixels are all done), whether or not the
+      pixel was still blending.
+
+    Each count comes from its own problem; neither changes an image."""
+    out = {}
+    for key, c, what in (("pairs", replace(cfg, tight_cut=False), U.EXPORT_PAIRS),
+                         ("visited", cfg, U.EXPORT_VISITED)):
+        r = Rasterizer(scenes, views, c, device=device)
+        r.problem.cfg.flags |= U.UBS_FLAG_COUNT_PAIRS
+        r.forward(check=True)
+        out[key] = r.export(what).to(torch.int64)
+        del r
+    return out
+
+
 def capture_steps(steps, device) -> torch.cuda.CUDAGraph:
     """One CUDA graph of forward+backward over several (rasterizer, dL)
     pairs, issued in order on one stream."""

@@ -36,6 +36,7 @@ UBS_ACT_EXP = 2
 
 EXPORT_KEYS, EXPORT_TILES, EXPORT_RECT, EXPORT_RECORDS, EXPORT_INSTANCES = 0, 1, 2, 3, 4
 EXPORT_TILE_START, EXPORT_FINAL_T, EXPORT_LAST, EXPORT_SCREEN_GRAD, EXPORT_PAIRS = 5, 6, 7, 8, 9
+EXPORT_VISITED = 10
 
 
 class ubs_scene(Structure):
@@ -99,6 +100,7 @@ SIGNATURES = {
                              POINTER(c_size_t), c_void_p]),
     "ubs_status_string": (c_char_p, [c_int32]),
     "ubs_render_fwd_static": (c_int32, [POINTER(ubs_problem), c_void_p, c_void_p]),
+    "ubs_read_status_static": (c_int32, [POINTER(ubs_problem), POINTER(ubs_device_status), c_void_p]),
     "ubs_loss_workspace_size": (c_size_t, [c_int32, POINTER(c_int32), POINTER(c_int32)]),
     "ubs_image_loss": (c_int32, [c_int32, POINTER(c_int32), POINTER(c_int32), c_void_p, c_void_p, c_float,
                                  c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -183,6 +185,14 @@ def ubs_status_string(status) -> str:
 
 def ubs_render_fwd_static(problem, image, stream) -> int:
     return int(load().ubs_render_fwd_static(ctypes.byref(problem), image, stream))
+
+
+def ubs_read_status_static(problem, stream) -> ubs_device_status:
+    out = ubs_device_status()
+    st = load().ubs_read_status_static(ctypes.byref(problem), ctypes.byref(out), stream)
+    if st != UBS_OK:
+        raise UBSError(st, "ubs_read_status_static")
+    return out
 
 
 def _sizes(widths, heights):

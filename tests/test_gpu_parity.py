@@ -3,7 +3,10 @@
 Bit-exact: culling, depth keys, tile rectangles, float32 conic/beta, sorted
 instance lists and tile ranges.  Images: maximum absolute error 1e-4 against
 float64 (admissible branches near thresholds).  Gradients: relative error
-1e-3 per parameter group against the oracle's autograd gradients.
+1e-3 per parameter group and element by element (plus 1e-6 of the group's
+largest) against the oracle's autograd gradients.  Pair counts (records
+with r < 1 met before a pixel terminates, the blend kernels' work unit)
+exact against the oracle's count.
 """
 import numpy as np
 import pytest
@@ -12,7 +15,7 @@ import torch
 from oracle import render64 as R64
 from paper_2510_03312_gb300 import scenes as S
 
-from parity_tools import check_bins, check_grads, check_images, check_preprocess, gpu_forward
+from parity_tools import check_bins, check_grads, check_images, check_pairs, check_preprocess, gpu_forward
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +62,17 @@ def test_forward_parity(case):
     check_bins(gpu, orc)
     worst, nflag, _ = check_images(gpu, orc, recs=recs)
     print(f"{case}: max image error {worst:.2e}, flagged pixels {nflag}")
+
+
+@pytest.mark.parametrize("case", ["static_small", "n3_ragged_2views", "n6_3views", "n7_3views", "n4_2views", "tile8",
+                                  "tile16x32"])
+def test_pair_counts(case):
+    """The counting variant of the forward against the oracle's tile-free
+    pair count, per pixel (lists built without the tight cut)."""
+    scenes, views, cfg = CASES[case]()
+    n_cmp, n_exact, total = check_pairs(scenes, views, cfg, tile_free=case == "static_small")
+    assert n_exact >= 0.99 * n_cmp and total > 0
+    print(f"{case}: {n_cmp} pixels, {n_exact} with one admissible count, {total} pairs")
 
 
 @pytest.mark.parametrize("case", ["n3_ragged_2views", "n3_skew", "n3_skew2", "n6_cayley_2views", "n7_chol_2views", "n3_exp",
@@ -201,6 +215,8 @@ def test_very_long_tile_lists():
     tiles = sorted(np.argsort(-counts)[:2].tolist())
     _, _, ref = check_images(gpu, orc, recs=recs, tiles=tiles)
     check_grads(gpu, orc, ref, tiles=tiles)
+    n_cmp, n_exact, total = check_pairs([sc], [v], cfg, tiles=tiles)
+    assert n_cmp > 0 and total > 0
 
 
 @pytest.mark.parametrize("n_views,N", [(40, 6), (256, 7), (40, 3)])
@@ -236,6 +252,10 @@ def test_full_size_static_sampled():
     worst, nflag, ref = check_images(gpu, orc, recs=recs, tiles=tiles)
     print(f"full size: max image error {worst:.2e} on {len(tiles)} tiles, flagged {nflag}")
     check_grads(gpu, orc, ref, tiles=tiles)
+    del gpu
+    n_cmp, n_exact, total = check_pairs(wl.scenes, wl.views, wl.cfg, tiles=tiles)
+    print(f"full size pair counts: {n_cmp} pixels, {n_exact} with one admissible count, {total} pairs")
+    assert n_exact >= 0.99 * n_cmp
 
 
 @pytest.mark.parametrize("make", [S.workload_view_dependent, S.workload_dynamic, S.workload_uneven_mix],

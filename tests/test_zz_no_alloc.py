@@ -67,3 +67,25 @@ def test_static_scratch_rejects_problems_larger_than_the_scratch():
     img = torch.zeros(3 * 4096 * 4096, dtype=torch.float32, device="cuda")
     st = U.ubs_render_fwd_static(r.problem, img.data_ptr(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == U.UBS_ERR_WORKSPACE
+
+
+def test_static_scratch_reports_a_capacity_overflow():
+    """With an instance capacity too small for the scene the image is left as
+    it was and the overflow, with the count needed, is read back from the
+    fixed scratch; with the capacity restored the same call renders again."""
+    r = _problem(73, 6000, 120, 90, 2)
+    ref = r.forward(check=False).clone()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    need = int(r.status().instances)
+    cap = r.problem.instance_capacity
+    r.problem.instance_capacity = need // 4
+    img = torch.full_like(r.image, float("nan"))
+    assert U.ubs_render_fwd_static(r.problem, img.data_ptr(), stream) == U.UBS_OK
+    st = U.ubs_read_status_static(r.problem, stream)
+    assert st.status == U.UBS_ERR_CAPACITY and st.instances == need
+    assert torch.isnan(img).all()
+    r.problem.instance_capacity = cap
+    out = _static_render(r)
+    st = U.ubs_read_status_static(r.problem, stream)
+    assert st.status == U.UBS_OK and st.instances == need
+    assert (out - ref).abs().max().item() <= TOL
