@@ -731,13 +731,14 @@ def bench_batched(dev, pk, n_sm, steps=5, warmup=2):
         plan = A.tune(wl.scenes, wl.views, wl.cfg, A.device_measure(ds, wl.views, wl.cfg, device=dev))
         t_tune = time.perf_counter() - t0
         from dataclasses import replace
-        cfg = replace(wl.cfg, tile_w=plan.tile[0], tile_h=plan.tile[1])
+        cfg = replace(wl.cfg, tile_w=plan.tile[0], tile_h=plan.tile[1], persistent=plan.persistent)
         b = raster.Batch(ds, wl.views, cfg, plan.groups, device=dev)
         b.size()
         dls = b.dL_like(1e-6)
         g = b.capture(dls)
         out["batched"] = entry(time_calls(g.replay, steps, warmup))
         out["batched"].update({"tile": f"{plan.tile[0]}x{plan.tile[1]}", "schedule": plan.schedule,
+                               "blend_launch": "persistent" if plan.persistent else "grid",
                                "launches": len(plan.groups), "captured_graph": True})
         out["autotune"] = {"seconds": round(t_tune, 1), "candidates_ms": plan.table}
         out["speedup_batched"] = round(out["per_view"]["ms_per_step"] / out["batched"]["ms_per_step"], 3)

@@ -85,10 +85,13 @@ enum {
   UBS_FLAG_COUNT_PAIRS = 2, /* diagnostic: ubs_render_fwd runs a variant that also counts,
                                per pixel, the pairs with r < 1 and the evaluated entries
                                (ubs_export 9 and 10) */
-  UBS_FLAG_ACCUMULATE_GRADS = 4 /* ubs_render_bwd / ubs_render_bwd_params ADD the parameter
+  UBS_FLAG_ACCUMULATE_GRADS = 4, /* ubs_render_bwd / ubs_render_bwd_params ADD the parameter
                                    gradients to the ubs_scene_grad buffers instead of
                                    overwriting them: a scene rendered by several problems
                                    (launches) gets the sum over all of its views */
+  UBS_FLAG_PERSISTENT = 8 /* the blend kernels run as persistent grids (one CTA per resident
+                             slot) that take tiles or 8x8 blocks from a counter in the same order,
+                             instead of one CTA per tile or block; the results are the same */
 };
 
 /* One primitive set (Sec. 4.1-4.3).  Structure of arrays: every block below

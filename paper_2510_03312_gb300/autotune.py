@@ -1,13 +1,15 @@
 """Tile shape and batch schedule selection for a batch of render jobs.
 
 A plan is a tile shape for the blend (one of the shapes the kernels are
-built for) and a schedule: a partition of the views into launches, each
-launch one problem over the scenes its views use.  Candidates are timed on
+built for), a launch form of the blend kernels (one CTA per tile or 8x8
+block, or a persistent grid that takes them from a counter) and a
+schedule: a partition of the views into launches, each launch one problem
+over the scenes its views use.  Candidates are timed on
 the device by replaying a captured CUDA graph of the whole forward+backward
 step, and the fastest is kept, cached under a signature of the batch's
 shapes.
 
-Neither choice changes the method's arithmetic: every pixel composites the
+None of these choices changes the method's arithmetic: every pixel composites the
 same records in the same (depth, index) order under any tile shape, and a
 scene's gradient is the sum over all of its views whichever launch renders
 them (Batch accumulates into one buffer per scene).  Only the float
@@ -22,6 +24,7 @@ import os
 from dataclasses import dataclass, field
 
 TILES = ((8, 8), (16, 16), (16, 32), (32, 32))
+FORMS = (False, True)  # blend launch form: grid, persistent
 MAX_VIEWS = 256  # views per problem accepted by the C-ABI
 
 
@@ -64,7 +67,7 @@ SCHEDULES = {
 }
 
 
-def signature(scenes, views, cfg, tiles, schedules) -> str:
+def signature(scenes, views, cfg, tiles, schedules, forms=FORMS) -> str:
     """Key of a batch's shapes: scene (N, rotation mode, P), view (W, H,
     scene), the config constants that change the work, and the candidates."""
     d = {
@@ -74,6 +77,7 @@ def signature(scenes, views, cfg, tiles, schedules) -> str:
                 float(cfg.near), bool(cfg.tight_cut)],
         "tiles": [list(t) for t in tiles],
         "schedules": sorted(schedules),
+        "forms": [bool(f) for f in forms],
     }
     return hashlib.sha256(json.dumps(d, sort_keys=True).encode()).hexdigest()[:24]
 
@@ -84,16 +88,17 @@ class Plan:
     schedule: str
     groups: list
     ms: float
-    table: dict = field(default_factory=dict)  # "WxH/schedule" -> ms
+    table: dict = field(default_factory=dict)  # "WxH/schedule[/persistent]" -> ms
+    persistent: bool = False
 
     def to_json(self):
         return {"tile": list(self.tile), "schedule": self.schedule, "groups": self.groups, "ms": self.ms,
-                "table": self.table}
+                "table": self.table, "persistent": self.persistent}
 
     @classmethod
     def from_json(cls, d):
         return cls(tuple(d["tile"]), d["schedule"], [list(g) for g in d["groups"]], float(d["ms"]),
-                   dict(d.get("table", {})))
+                   dict(d.get("table", {})), bool(d.get("persistent", False)))
 
 
 class PlanCache:
@@ -118,13 +123,15 @@ class PlanCache:
             os.replace(tmp, self.path)
 
 
-def tune(scenes, views, cfg, measure, tiles=TILES, schedules=None, cache: PlanCache | None = None) -> Plan:
-    """Times every (tile, schedule) candidate with ``measure(tile, groups)``
-    (milliseconds per forward+backward step) and returns the fastest plan.
-    ``scenes`` need ``N``, ``rot_mode`` and ``P``; ``views`` need ``width``,
-    ``height`` and ``scene_id``.  Ties go to the earlier candidate."""
+def tune(scenes, views, cfg, measure, tiles=TILES, schedules=None, cache: PlanCache | None = None,
+         forms=FORMS) -> Plan:
+    """Times every (tile, schedule, launch form) candidate with
+    ``measure(tile, groups, persistent)`` (milliseconds per forward+backward
+    step) and returns the fastest plan.  ``scenes`` need ``N``,
+    ``rot_mode`` and ``P``; ``views`` need ``width``, ``height`` and
+    ``scene_id``.  Ties go to the earlier candidate."""
     schedules = SCHEDULES if schedules is None else schedules
-    key = signature(scenes, views, cfg, tiles, schedules)
+    key = signature(scenes, views, cfg, tiles, schedules, forms)
     if cache is not None:
         hit = cache.get(key)
         if hit is not None:
@@ -133,10 +140,11 @@ def tune(scenes, views, cfg, measure, tiles=TILES, schedules=None, cache: PlanCa
     for tile in tiles:
         for name, make in schedules.items():
             groups = make(scenes, views)
-            ms = float(measure(tuple(tile), groups))
-            table[f"{tile[0]}x{tile[1]}/{name}"] = round(ms, 4)
-            if best is None or ms < best.ms:
-                best = Plan(tuple(tile), name, groups, ms)
+            for persistent in forms:
+                ms = float(measure(tuple(tile), groups, bool(persistent)))
+                table[f"{tile[0]}x{tile[1]}/{name}" + ("/persistent" if persistent else "")] = round(ms, 4)
+                if best is None or ms < best.ms:
+                    best = Plan(tuple(tile), name, groups, ms, persistent=bool(persistent))
     if best is None:
         raise ValueError("no candidates")
     best.table = table
@@ -157,8 +165,8 @@ def device_measure(scenes, views, cfg, device="cuda", steps=3, warmup=1):
 
     from .raster import Batch
 
-    def measure(tile, groups):
-        c = replace(cfg, tile_w=int(tile[0]), tile_h=int(tile[1]))
+    def measure(tile, groups, persistent=False):
+        c = replace(cfg, tile_w=int(tile[0]), tile_h=int(tile[1]), persistent=bool(persistent))
         b = Batch(scenes, views, c, groups, device=device)
         b.size()
         dls = b.dL_like(1e-6)

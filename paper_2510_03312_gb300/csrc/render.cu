@@ -33,6 +33,8 @@
 // (reduce-scatter: 12 shuffles for the 10 values, leaving each total in one
 // lane), and one vector atomic add per (record, block) flushes the sum --
 // never one global atomic per pixel.
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace ubs {
@@ -54,6 +56,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 // Packed float32 pairs (sm_100 and later): one instruction rounds each half
@@ -82,17 +89,20 @@ __device__ __forceinline__ void stage_record(const float4* __restrict__ rec4, ui
   st.s = make_float2(d.z, d.w);
   // conservative box of the pixels with alpha >= alpha_min: the ellipse
   // r <= r_cut, r_cut = 1 - (alpha_min/o(q))^(1/beta_x), widened by 2% + 0.02
-  // in r_cut and 0.1 px; empty when o(q) < alpha_min
+  // in r_cut and 0.1 px; empty when o(q) < alpha_min.  Approximate
+  // reciprocals and square roots (relative errors near 1e-7) are far inside
+  // those margins.
   const float det = c.x * c.z - c.y * c.y;
-  const float s00 = c.z / det, s11 = c.x / det;
-  float rc = 1.0f - ex2_approx((lg2_amin - c.w) / d.x);
+  const float idet = rcp_approx(det);
+  const float s00 = c.z * idet, s11 = c.x * idet;
+  float rc = 1.0f - ex2_approx((lg2_amin - c.w) * rcp_approx(d.x));
   if (!(rc > -0.02f)) {
     box = make_float4(1.0f, -1.0f, 1.0f, -1.0f);
     rcut = -1.0f;
   } else {
     rc = fminf(1.0f, fmaf(rc, 1.02f, 0.02f));
     rcut = rc;
-    const float ex = sqrtf(fmaxf(rc * s00, 0.0f)) + 0.1f, ey = sqrtf(fmaxf(rc * s11, 0.0f)) + 0.1f;
+    const float ex = sqrt_approx(fmaxf(rc * s00, 0.0f)) + 0.1f, ey = sqrt_approx(fmaxf(rc * s11, 0.0f)) + 0.1f;
     box = make_float4(st.p.x - ex, st.p.x + ex, st.p.y - ey, st.p.y + ey);
   }
 }
@@ -101,8 +111,9 @@ __device__ __forceinline__ void stage_record(const float4* __restrict__ rec4, ui
 // one packed instruction serves a lane's two pixels (rows y and y + 4 of
 // its column): A = (-mx, -mx, -my, -my), Bc = (a, a, 2b, 2b),
 // Cc = (c, c, beta_x, beta_x), D = (log2 o(q), log2 o(q), red, red),
-// E = (green, green, blue, blue).
-struct Staged2 {
+// E = (green, green, blue, blue).  Kept as one 80-byte structure per entry
+// in shared memory, so that an entry's five loads share one address.
+struct __align__(16) Staged2 {
   float4 A, Bc, Cc, D, E;
 };
 __device__ __forceinline__ Staged2 pack_staged(const Staged& st) {
@@ -199,9 +210,8 @@ __device__ __forceinline__ bool ellipse_hits(const float4& p, float c, float rcu
 // Each warp lists, in order, the staged entries j < n whose support meets
 // its block (all of them when `all`), from the packed staging of the
 // two-pixel kernels; returns the count.
-__device__ __forceinline__ int warp_cull_list2(const float4* s_bb, const float4* s_A, const float4* s_B,
-                                               const float4* s_C, const float* s_rc, int n, bool all, float x0,
-                                               float x1, float y0, float y1, uint8_t* list) {
+__device__ __forceinline__ int warp_cull_list2(const float4* s_bb, const Staged2* s_st, const float* s_rc, int n,
+                                               bool all, float x0, float x1, float y0, float y1, uint8_t* list) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int cnt = 0;
@@ -209,8 +219,8 @@ __device__ __forceinline__ int warp_cull_list2(const float4* s_bb, const float4*
     const int j = k + lane;
     bool hit = j < n && (all || box_hits(s_bb[j], x0, x1, y0, y1));
     if (hit && !all) {
-      const float4 A = s_A[j], Bc = s_B[j];
-      hit = ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), s_C[j].x, s_rc[j], x0, x1, y0, y1);
+      const float4 A = s_st[j].A, Bc = s_st[j].Bc;
+      hit = ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), s_st[j].Cc.x, s_rc[j], x0, x1, y0, y1);
     }
     const unsigned m = __ballot_sync(kFull, hit);
     if (hit) list[cnt + __popc(m & lt)] = (uint8_t)j;
@@ -226,30 +236,50 @@ __device__ __forceinline__ int warp_cull_list2(const float4* s_bb, const float4*
 // takes the operations of the scalar rule above in the same order.  The
 // warp walks its list two entries per step between checks that its 64
 // pixels are all done; the CTA stops loading batches once its tile's are.
+template <int TW, int TH>
+struct FwdSmem {
+  static constexpr int NT = TW * TH / 2;           // threads: two pixels each
+  static constexpr int BS = NT < 256 ? NT : 256;  // records staged per batch
+  static constexpr int NW = NT / 32;
+  Staged2 st[BS];
+  float4 bb[BS];
+  float rc[BS];
+  uint8_t list[NW][BS];
+  int v;
+  uint32_t next;
+};
+
+struct FwdArgs {
+  const ViewDev* __restrict__ views;
+  int V;
+  CfgDev cfg;
+  const uint32_t* __restrict__ tstart;
+  const uint32_t* __restrict__ ivals;
+  const float4* __restrict__ rec4;
+  float* __restrict__ image;
+  float* __restrict__ Tfin;
+  uint32_t* __restrict__ lastc;
+  const Header* hdr;
+  uint32_t R;
+  uint32_t* __restrict__ pairs;
+  uint32_t* __restrict__ visited;
+  const uint32_t* __restrict__ tile_order;
+  uint32_t n_tiles, cap;
+  uint32_t* queue;  // persistent form: [next tile, finished CTAs], zero between launches
+};
+
+// One tile g, by the whole CTA (every thread calls it).
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW * TH / 2) : 16))
-    render_fwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
-                      const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
-                      float* __restrict__ image, float* __restrict__ Tfin, uint32_t* __restrict__ lastc,
-                      const Header* hdr, uint32_t R, uint32_t* __restrict__ pairs, uint32_t* __restrict__ visited,
-                      const uint32_t* __restrict__ tile_order, uint32_t n_tiles, uint32_t cap) {
-  wait_prior_grid();
-  constexpr int NT = TW * TH / 2;           // threads: two pixels each
-  constexpr int BS = NT < 256 ? NT : 256;  // records staged per batch
-  constexpr int NW = NT / 32;
-  __shared__ float4 s_A[BS], s_B[BS], s_C[BS], s_D[BS], s_E[BS], s_bb[BS];
-  __shared__ float s_rc[BS];
-  __shared__ uint8_t s_list[NW][BS];
-  __shared__ int s_v;
-  if (hdr->status != 0) return;
-  const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x] : blockIdx.x;
-  const uint32_t start = tstart[g], end = tstart[g + 1];  // loaded while warp 0 finds the view
+__device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<TW, TH>& sm) {
+  constexpr int NT = FwdSmem<TW, TH>::NT, BS = FwdSmem<TW, TH>::BS;
+  const CfgDev& cfg = A.cfg;
+  const uint32_t start = A.tstart[g], end = A.tstart[g + 1];  // loaded while warp 0 finds the view
   if (threadIdx.x < 32) {
-    const int vi = find_view_warp(views, V, g);
-    if (threadIdx.x == 0) s_v = vi;
+    const int vi = find_view_warp(A.views, A.V, g);
+    if (threadIdx.x == 0) sm.v = vi;
   }
   __syncthreads();
-  const ViewDev& v = views[s_v];
+  const ViewDev& v = A.views[sm.v];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
   int lx, ly, bx, by;
@@ -262,7 +292,7 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
   const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 7.0f;
   const float lg2_amin = lg2_approx(cfg.amin);
   const float2 one = make_float2(1.0f, 1.0f), neg1 = make_float2(-1.0f, -1.0f);
-  uint8_t* list = s_list[threadIdx.x >> 5];
+  uint8_t* list = sm.list[threadIdx.x >> 5];
   float2 T = one, C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0;
   uint32_t last0 = 0, last1 = 0, np0 = 0, np1 = 0, nv = 0;
   bool done0 = !in0, done1 = !in1;
@@ -272,35 +302,31 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
     if (threadIdx.x < BS && idx < end) {
       Staged st;
       float4 box;
-      stage_record(rec4, min(ivals[idx], R - 1), ox, oy, lg2_amin, st, box, s_rc[threadIdx.x]);  // ids < R
-      const Staged2 s2 = pack_staged(st);
-      s_A[threadIdx.x] = s2.A;
-      s_B[threadIdx.x] = s2.Bc;
-      s_C[threadIdx.x] = s2.Cc;
-      s_D[threadIdx.x] = s2.D;
-      s_E[threadIdx.x] = s2.E;
-      s_bb[threadIdx.x] = box;
+      stage_record(A.rec4, min(A.ivals[idx], A.R - 1), ox, oy, lg2_amin, st, box, sm.rc[threadIdx.x]);  // ids < R
+      sm.st[threadIdx.x] = pack_staged(st);
+      sm.bb[threadIdx.x] = box;
     }
     __syncthreads();
     const int n = (int)min((uint32_t)BS, end - base);
     // the counting variant walks every entry, to count every pair with r < 1,
     // and also counts the entries the cull would have kept (visited)
-    const int cnt = warp_cull_list2(s_bb, s_A, s_B, s_C, s_rc, n, COUNT, wx0, wx1, wy0, wy1, list);
+    const int cnt = warp_cull_list2(sm.bb, sm.st, sm.rc, n, COUNT, wx0, wx1, wy0, wy1, list);
     const uint32_t rel = base - start;
     // one entry for both pixels; branch-free: a pair that is skipped (or
     // stops its pixel) adds c * 0 and keeps T, which leaves C and T exactly
     auto blend = [&](int j) {
-      const float4 D = s_D[j];
+      const Staged2& sj = sm.st[j];
+      const float4 D = sj.D;
       PairEval2 e;
-      eval_pair2<false>(fx, fy, s_A[j], s_B[j], s_C[j], D, cfg.amax, e);
+      eval_pair2<false>(fx, fy, sj.A, sj.Bc, sj.Cc, D, cfg.amax, e);
       const float2 r = e.r;
       const float al0 = e.alpha.x, al1 = e.alpha.y;
       if constexpr (COUNT) {
         np0 += (!done0 && r.x < 1.0f);
         np1 += (!done1 && r.y < 1.0f);
-        const float4 A = s_A[j], Bc = s_B[j];
-        nv += box_hits(s_bb[j], wx0, wx1, wy0, wy1) &&
-              ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), s_C[j].x, s_rc[j], wx0, wx1, wy0, wy1);
+        const float4 A = sj.A, Bc = sj.Bc;
+        nv += box_hits(sm.bb[j], wx0, wx1, wy0, wy1) &&
+              ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), sj.Cc.x, sm.rc[j], wx0, wx1, wy0, wy1);
       }
       const bool u0 = !done0 && r.x < 1.0f && al0 >= cfg.amin;
       const bool u1 = !done1 && r.y < 1.0f && al1 >= cfg.amin;
@@ -313,7 +339,7 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
       float2 w = mul2(a, T);
       w.x = ok0 ? w.x : 0.0f;
       w.y = ok1 ? w.y : 0.0f;
-      const float4 E = s_E[j];
+      const float4 E = sj.E;
       C0 = fma2(hi2(D), w, C0);
       C1 = fma2(lo2(E), w, C1);
       C2 = fma2(hi2(E), w, C2);
@@ -329,17 +355,17 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
     }
   }
   const size_t plane = (size_t)v.W * v.H;
-  float* img = image + (size_t)v.pix_off * 3;
+  float* img = A.image + (size_t)v.pix_off * 3;
   if (in0) {
     const size_t pix = (size_t)y0 * v.W + x;
     img[pix] = fmaf(T.x, cfg.bg[0], C0.x);
     img[plane + pix] = fmaf(T.x, cfg.bg[1], C1.x);
     img[2 * plane + pix] = fmaf(T.x, cfg.bg[2], C2.x);
-    Tfin[v.pix_off + pix] = T.x;
-    lastc[v.pix_off + pix] = last0;
+    A.Tfin[v.pix_off + pix] = T.x;
+    A.lastc[v.pix_off + pix] = last0;
     if constexpr (COUNT) {
-      pairs[v.pix_off + pix] = np0;
-      visited[v.pix_off + pix] = nv;
+      A.pairs[v.pix_off + pix] = np0;
+      A.visited[v.pix_off + pix] = nv;
     }
   }
   if (in1) {
@@ -347,12 +373,49 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
     img[pix] = fmaf(T.y, cfg.bg[0], C0.y);
     img[plane + pix] = fmaf(T.y, cfg.bg[1], C1.y);
     img[2 * plane + pix] = fmaf(T.y, cfg.bg[2], C2.y);
-    Tfin[v.pix_off + pix] = T.y;
-    lastc[v.pix_off + pix] = last1;
+    A.Tfin[v.pix_off + pix] = T.y;
+    A.lastc[v.pix_off + pix] = last1;
     if constexpr (COUNT) {
-      pairs[v.pix_off + pix] = np1;
-      visited[v.pix_off + pix] = nv;
+      A.pairs[v.pix_off + pix] = np1;
+      A.visited[v.pix_off + pix] = nv;
     }
+  }
+}
+
+// The grid form: one CTA per tile, in bin_sort's tile order where the lists
+// are dense.
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW * TH / 2) : 16))
+    render_fwd_kernel(FwdArgs A) {
+  wait_prior_grid();
+  __shared__ FwdSmem<TW, TH> sm;
+  if (A.hdr->status != 0) return;
+  const uint32_t g =
+      A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[blockIdx.x] : blockIdx.x;
+  fwd_tile<TW, TH, COUNT>(A, g, sm);
+}
+
+// The persistent form: as many CTAs as fit on the GPU at once, each taking
+// the next tile (same order) from a counter until none is left.  No CTA
+// waits on another; the last CTA to finish resets the counters for the
+// next launch.
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW * TH / 2) : 16))
+    render_fwd_persistent_kernel(FwdArgs A) {
+  wait_prior_grid();
+  __shared__ FwdSmem<TW, TH> sm;
+  if (A.hdr->status != 0) return;
+  const bool dense = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap);
+  for (;;) {
+    if (threadIdx.x == 0) sm.next = atomicAdd(A.queue, 1u);
+    __syncthreads();  // also: every thread is done with the previous tile's shared memory
+    const uint32_t t = sm.next;
+    if (t >= A.n_tiles) break;
+    fwd_tile<TW, TH, COUNT>(A, dense ? A.tile_order[t] : t, sm);
+  }
+  if (threadIdx.x == 0 && atomicAdd(A.queue + 1, 1u) == gridDim.x - 1) {
+    A.queue[0] = 0;  // every CTA has taken its last tile
+    A.queue[1] = 0;
   }
 }
 
@@ -415,29 +478,43 @@ __device__ __forceinline__ int writer_of(int lane) {
 // evaluation and the per-pixel recurrences (T, the colour behind) run in
 // packed pairs over the lane's two pixels; the two share dx, so a lane's
 // sums of q dx, q dx^2 and q dx dy take dx out of the sum.
+struct BwdSmem {
+  static constexpr int WB = 32;  // entries per batch: one per lane
+  Staged2 st[WB];
+  uint32_t rec[WB];
+  float acc[10][WB + 1];  // +1: the 10 writer lanes hit 10 different banks
+  uint8_t list[WB];
+};
+
+struct BwdArgs {
+  const ViewDev* __restrict__ views;
+  int V;
+  CfgDev cfg;
+  const uint32_t* __restrict__ tstart;
+  const uint32_t* __restrict__ ivals;
+  const float4* __restrict__ rec4;
+  const float* __restrict__ dLdimg;
+  const float* __restrict__ Tfin;
+  const uint32_t* __restrict__ lastc;
+  float4* __restrict__ g2d;
+  const Header* hdr;
+  uint32_t R;
+  const uint32_t* __restrict__ tile_order;
+  uint32_t n_tiles, cap;
+  uint32_t* queue;  // persistent form: [next block, finished CTAs], zero between launches
+};
+
+// One 8x8 block wb of tile g, by one warp.
 template <int TW, int TH>
-__global__ void __launch_bounds__(32)
-    render_bwd_kernel(const ViewDev* __restrict__ views, int V, CfgDev cfg, const uint32_t* __restrict__ tstart,
-                      const uint32_t* __restrict__ ivals, const float4* __restrict__ rec4,
-                      const float* __restrict__ dLdimg, const float* __restrict__ Tfin,
-                      const uint32_t* __restrict__ lastc, float4* __restrict__ g2d, const Header* hdr, uint32_t R,
-                      const uint32_t* __restrict__ tile_order, uint32_t n_tiles, uint32_t cap) {
-  wait_prior_grid();
-  constexpr int WB = 32;             // entries per batch: one per lane
-  constexpr int BPT = TW * TH / 64;  // 8x8 blocks per tile
-  constexpr int WPR = TW / 8;        // blocks per row of the tile
-  __shared__ float4 s_A[WB], s_B[WB], s_C[WB], s_D[WB], s_E[WB];
-  __shared__ uint32_t s_rec[WB];
-  __shared__ float s_acc[10][WB + 1];  // +1: the 10 writer lanes hit 10 different banks
-  __shared__ uint8_t s_list[WB];
-  if (hdr->status != 0) return;
-  const uint32_t g = tile_order && order_dense(hdr, n_tiles, cap) ? tile_order[blockIdx.x / BPT] : blockIdx.x / BPT;
-  const int wb = blockIdx.x % BPT;
-  const int lane = threadIdx.x;
-  const uint32_t start = tstart[g], end = tstart[g + 1];  // loaded while the view is found
-  const int vi = find_view_warp(views, V, g);
+__device__ __forceinline__ void bwd_block(const BwdArgs& A, uint32_t g, int wb, BwdSmem& sm) {
+  constexpr int WB = BwdSmem::WB;
+  constexpr int WPR = TW / 8;  // blocks per row of the tile
+  const CfgDev& cfg = A.cfg;
+  const int lane = threadIdx.x & 31;
+  const uint32_t start = A.tstart[g], end = A.tstart[g + 1];  // loaded while the view is found
+  const int vi = find_view_warp(A.views, A.V, g);
   if (start == end) return;  // an empty list: no pixel of the tile has a contributor
-  const ViewDev& v = views[vi];
+  const ViewDev& v = A.views[vi];
   const uint32_t lt = g - v.tile_off;
   const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
   const int bx = (wb % WPR) * 8, by = (wb / WPR) * 8;
@@ -453,23 +530,23 @@ __global__ void __launch_bounds__(32)
   uint32_t last0 = 0, last1 = 0;
   {
     const size_t plane = (size_t)v.W * v.H;
-    const float* gi = dLdimg + (size_t)v.pix_off * 3;
+    const float* gi = A.dLdimg + (size_t)v.pix_off * 3;
     const int y0 = ty * TH + ly, y1 = y0 + 4;
     if (x < v.W && y0 < v.H) {
       const size_t pix = (size_t)y0 * v.W + x;
       G0.x = gi[pix];
       G1.x = gi[plane + pix];
       G2.x = gi[2 * plane + pix];
-      T.x = Tfin[v.pix_off + pix];
-      last0 = lastc[v.pix_off + pix];
+      T.x = A.Tfin[v.pix_off + pix];
+      last0 = A.lastc[v.pix_off + pix];
     }
     if (x < v.W && y1 < v.H) {
       const size_t pix = (size_t)y1 * v.W + x;
       G0.y = gi[pix];
       G1.y = gi[plane + pix];
       G2.y = gi[2 * plane + pix];
-      T.y = Tfin[v.pix_off + pix];
-      last1 = lastc[v.pix_off + pix];
+      T.y = A.Tfin[v.pix_off + pix];
+      last1 = A.lastc[v.pix_off + pix];
     }
   }
   const uint32_t wlast = __reduce_max_sync(kFull, max(last0, last1));
@@ -484,32 +561,31 @@ __global__ void __launch_bounds__(32)
     const int n = hi - lo;
     bool listed = false;
     if (lane < n) {
-      const uint32_t r = min(ivals[start + lo + lane], R - 1);  // ids are < R by construction
+      const uint32_t r = min(A.ivals[start + lo + lane], A.R - 1);  // ids are < R by construction
       Staged st;
       float4 box;
       float rc;
-      stage_record(rec4, r, ox, oy, lg2_amin, st, box, rc);
-      s_rec[lane] = r;
-      const Staged2 s2 = pack_staged(st);
-      s_A[lane] = s2.A;
-      s_B[lane] = s2.Bc;
-      s_C[lane] = s2.Cc;
-      s_D[lane] = s2.D;
-      s_E[lane] = s2.E;
+      stage_record(A.rec4, r, ox, oy, lg2_amin, st, box, rc);
+      sm.rec[lane] = r;
+      sm.st[lane] = pack_staged(st);
       listed = box_hits(box, wx0, wx1, wy0, wy1) && ellipse_hits(st.p, st.q.x, rc, wx0, wx1, wy0, wy1);
     }
     const unsigned lm = __ballot_sync(kFull, listed);
-    if (listed) s_list[__popc(lm & ((1u << lane) - 1u))] = (uint8_t)lane;
+    if (listed) sm.list[__popc(lm & ((1u << lane) - 1u))] = (uint8_t)lane;
     __syncwarp();
     unsigned touched = 0;  // entries the block used (warp-uniform)
+    // entry j of the batch is list position lo + j: the forward composited it
+    // at a pixel only if lo + j < that pixel's last contributor
+    const int lim0 = (int)last0 - lo, lim1 = (int)last1 - lo;
     for (int i = __popc(lm) - 1; i >= 0; --i) {
-      const int j = s_list[i];
-      const float4 D = s_D[j], E = s_E[j];
+      const int j = sm.list[i];
+      const Staged2& sj = sm.st[j];
+      const float4 D = sj.D, E = sj.E;
       PairEval2 e;
-      eval_pair2<true>(fx, fy, s_A[j], s_B[j], s_C[j], D, cfg.amax, e);
+      eval_pair2<true>(fx, fy, sj.A, sj.Bc, sj.Cc, D, cfg.amax, e);
       // pairs the forward composited
-      const bool use0 = e.r.x < 1.0f && e.alpha.x >= cfg.amin && (uint32_t)(lo + j) < last0;
-      const bool use1 = e.r.y < 1.0f && e.alpha.y >= cfg.amin && (uint32_t)(lo + j) < last1;
+      const bool use0 = e.r.x < 1.0f && e.alpha.x >= cfg.amin && j < lim0;
+      const bool use1 = e.r.y < 1.0f && e.alpha.y >= cfg.amin && j < lim1;
       const unsigned hits = __ballot_sync(kFull, use0 || use1);
       if (hits == 0) continue;  // no pixel of the block: T and B stay
       touched |= 1u << j;
@@ -550,25 +626,65 @@ __global__ void __launch_bounds__(32)
       if (__popc(hits) == 1) {  // one lane: its values are the totals
         if (use0 || use1) {
 #pragma unroll
-          for (int m = 0; m < 10; ++m) s_acc[m][j] = gv[m];
+          for (int m = 0; m < 10; ++m) sm.acc[m][j] = gv[m];
         }
       } else {
         const float tot = warp_reduce10(gv, lane);
-        if (wslot >= 0) s_acc[wslot][j] = tot;
+        if (wslot >= 0) sm.acc[wslot][j] = tot;
       }
     }
     __syncwarp();
     if ((touched >> lane) & 1u) {
-      const float a = s_B[lane].x, b = 0.5f * s_B[lane].z, c = s_C[lane].x, beta = s_C[lane].z;
-      const float v0 = s_acc[0][lane], v1 = s_acc[1][lane];
-      float4* dst = g2d + 3 * (size_t)s_rec[lane];
+      const float a = sm.st[lane].Bc.x, b = 0.5f * sm.st[lane].Bc.z, c = sm.st[lane].Cc.x, beta = sm.st[lane].Cc.z;
+      const float v0 = sm.acc[0][lane], v1 = sm.acc[1][lane];
+      float4* dst = A.g2d + 3 * (size_t)sm.rec[lane];
       atomicAdd(dst, make_float4(2.0f * beta * (a * v0 + b * v1), 2.0f * beta * (b * v0 + c * v1),
-                                 -beta * s_acc[2][lane], -2.0f * beta * s_acc[3][lane]));
-      atomicAdd(dst + 1, make_float4(-beta * s_acc[4][lane], kLn2f * s_acc[5][lane], kLn2f * s_acc[6][lane],
-                                     s_acc[7][lane]));
-      atomicAdd((float2*)(dst + 2), make_float2(s_acc[8][lane], s_acc[9][lane]));
+                                 -beta * sm.acc[2][lane], -2.0f * beta * sm.acc[3][lane]));
+      atomicAdd(dst + 1, make_float4(-beta * sm.acc[4][lane], kLn2f * sm.acc[5][lane], kLn2f * sm.acc[6][lane],
+                                     sm.acc[7][lane]));
+      atomicAdd((float2*)(dst + 2), make_float2(sm.acc[8][lane], sm.acc[9][lane]));
     }
     __syncwarp();
+  }
+}
+
+// The grid form: one single-warp CTA per 8x8 block.
+template <int TW, int TH>
+__global__ void __launch_bounds__(32, 32)  // 64 registers: 32 one-warp CTAs per SM
+    render_bwd_kernel(BwdArgs A) {
+  wait_prior_grid();
+  constexpr int BPT = TW * TH / 64;  // 8x8 blocks per tile
+  __shared__ BwdSmem sm;
+  if (A.hdr->status != 0) return;
+  const uint32_t t = blockIdx.x / BPT;
+  const uint32_t g = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[t] : t;
+  bwd_block<TW, TH>(A, g, blockIdx.x % BPT, sm);
+}
+
+// The persistent form: as many one-warp CTAs as fit on the GPU at once, each
+// taking the next 8x8 block (same order) from a counter until none is left;
+// the last CTA to finish resets the counters for the next launch.
+template <int TW, int TH>
+__global__ void __launch_bounds__(32, 32)
+    render_bwd_persistent_kernel(BwdArgs A) {
+  wait_prior_grid();
+  constexpr int BPT = TW * TH / 64;
+  __shared__ BwdSmem sm;
+  if (A.hdr->status != 0) return;
+  const bool dense = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap);
+  const uint32_t n_blocks = A.n_tiles * BPT;
+  for (;;) {
+    uint32_t b = 0;
+    if (threadIdx.x == 0) b = atomicAdd(A.queue, 1u);
+    b = __shfl_sync(kFull, b, 0);
+    if (b >= n_blocks) break;
+    const uint32_t t = b / BPT;
+    bwd_block<TW, TH>(A, dense ? A.tile_order[t] : t, b % BPT, sm);
+    __syncwarp();
+  }
+  if (threadIdx.x == 0 && atomicAdd(A.queue + 1, 1u) == gridDim.x - 1) {
+    A.queue[0] = 0;  // every CTA has taken its last block
+    A.queue[1] = 0;
   }
 }
 
@@ -586,35 +702,88 @@ __global__ void __launch_bounds__(256) zero_visible_grads_kernel(const uint32_t*
   g2d[3 * (size_t)r + 2] = z;
 }
 
+// CTAs of `kernel` (with `threads` threads each) that fit on the current
+// device at once, for the persistent forms; 0 if the query fails.  Cached per
+// kernel and device.
+template <typename Kernel>
+uint32_t resident_ctas(Kernel kernel, int threads) {
+  static std::atomic<uint32_t> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  uint32_t n = cache[dev].load(std::memory_order_relaxed);
+  if (n) return n;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  n = (uint32_t)(per_sm > 0 ? per_sm : 0) * (uint32_t)(sms > 0 ? sms : 0);
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+template <int TW, int TH, bool COUNT>
+cudaError_t fwd_launch(const FwdArgs& args, const Layout& L, bool persistent, cudaStream_t st) {
+  constexpr int NT = TW * TH / 2;
+  if (persistent) {
+    const uint32_t n = resident_ctas(render_fwd_persistent_kernel<TW, TH, COUNT>, NT);
+    if (n > 0)
+      return launch_dependent(render_fwd_persistent_kernel<TW, TH, COUNT>, dim3(n < L.NT ? n : L.NT), dim3(NT), 0,
+                              st, args);
+  }
+  return launch_dependent(render_fwd_kernel<TW, TH, COUNT>, dim3(L.NT), dim3(NT), 0, st, args);
+}
+
 template <int TW, int TH>
 cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cudaStream_t st) {
-  const ViewDev* views = (const ViewDev*)(ws + L.views);
-  const uint32_t* tstart = (const uint32_t*)(ws + L.tstart);
-  const float4* rec4 = (const float4*)(ws + L.rec4);
-  float* Tfin = (float*)(ws + L.Tfin);
-  uint32_t* last = (uint32_t*)(ws + L.last);
-  const Header* hdr = (const Header*)(ws + L.header);
-  const uint32_t R = L.R > 0 ? L.R : 1;
-  constexpr int NT = TW * TH;
-  const uint32_t* order = order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr;
-  if (cfg.flags & 2)  // diagnostic variant: also count, per pixel, the pairs with r < 1 and the visited entries
-    launch_dependent(render_fwd_kernel<TW, TH, true>, dim3(L.NT), dim3(NT / 2), 0, st, views, L.V, cfg, tstart,
-                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, (uint32_t*)(ws + L.pairs),
-                     (uint32_t*)(ws + L.pairs) + L.NPIX, order, L.NT, L.cap);
-  else
-    launch_dependent(render_fwd_kernel<TW, TH, false>, dim3(L.NT), dim3(NT / 2), 0, st, views, L.V, cfg, tstart,
-                     sorted_instances(L, ws), rec4, image, Tfin, last, hdr, R, nullptr, nullptr, order, L.NT,
-                     L.cap);
-  return cudaGetLastError();
+  FwdArgs a;
+  a.views = (const ViewDev*)(ws + L.views);
+  a.V = L.V;
+  a.cfg = cfg;
+  a.tstart = (const uint32_t*)(ws + L.tstart);
+  a.ivals = sorted_instances(L, ws);
+  a.rec4 = (const float4*)(ws + L.rec4);
+  a.image = image;
+  a.Tfin = (float*)(ws + L.Tfin);
+  a.lastc = (uint32_t*)(ws + L.last);
+  a.hdr = (const Header*)(ws + L.header);
+  a.R = L.R > 0 ? L.R : 1;
+  const bool count = (cfg.flags & 2) != 0;  // diagnostic variant: also count pairs and visited entries
+  a.pairs = count ? (uint32_t*)(ws + L.pairs) : nullptr;
+  a.visited = count ? (uint32_t*)(ws + L.pairs) + L.NPIX : nullptr;
+  a.tile_order = order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr;
+  a.n_tiles = L.NT;
+  a.cap = L.cap;
+  a.queue = ((Header*)(ws + L.header))->ctr;
+  const bool persistent = (cfg.flags & 8) != 0;
+  return count ? fwd_launch<TW, TH, true>(a, L, persistent, st) : fwd_launch<TW, TH, false>(a, L, persistent, st);
 }
 
 template <int TW, int TH>
 cudaError_t bwd_t(const Layout& L, const CfgDev& cfg, char* ws, const float* dL, cudaStream_t st) {
-  launch_dependent(render_bwd_kernel<TW, TH>, dim3(L.NT * (TW * TH / 64)), dim3(32), 0, st, 
-      (const ViewDev*)(ws + L.views), L.V, cfg, (const uint32_t*)(ws + L.tstart), sorted_instances(L, ws),
-      (const float4*)(ws + L.rec4), dL, (const float*)(ws + L.Tfin), (const uint32_t*)(ws + L.last),
-      (float4*)(ws + L.g2d), (const Header*)(ws + L.header), L.R > 0 ? L.R : 1,
-      order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr, L.NT, L.cap);
+  BwdArgs a;
+  a.views = (const ViewDev*)(ws + L.views);
+  a.V = L.V;
+  a.cfg = cfg;
+  a.tstart = (const uint32_t*)(ws + L.tstart);
+  a.ivals = sorted_instances(L, ws);
+  a.rec4 = (const float4*)(ws + L.rec4);
+  a.dLdimg = dL;
+  a.Tfin = (const float*)(ws + L.Tfin);
+  a.lastc = (const uint32_t*)(ws + L.last);
+  a.g2d = (float4*)(ws + L.g2d);
+  a.hdr = (const Header*)(ws + L.header);
+  a.R = L.R > 0 ? L.R : 1;
+  a.tile_order = order_possible(L) ? (const uint32_t*)(ws + L.tile_order) : nullptr;
+  a.n_tiles = L.NT;
+  a.cap = L.cap;
+  a.queue = ((Header*)(ws + L.header))->ctr + 2;
+  const uint32_t n_blocks = L.NT * (TW * TH / 64);
+  if (cfg.flags & 8) {
+    const uint32_t n = resident_ctas(render_bwd_persistent_kernel<TW, TH>, 32);
+    if (n > 0)
+      return launch_dependent(render_bwd_persistent_kernel<TW, TH>, dim3(n < n_blocks ? n : n_blocks), dim3(32), 0,
+                              st, a);
+  }
+  launch_dependent(render_bwd_kernel<TW, TH>, dim3(n_blocks), dim3(32), 0, st, a);
   return cudaGetLastError();
 }
 

@@ -131,6 +131,7 @@ class RasterConfig:
     bg: tuple = (0.0, 0.0, 0.0)
     tight_cut: bool = True
     jac_clip: float = 1.3
+    persistent: bool = False  # launch form of the blend kernels (a schedule, not arithmetic)
 
 
 # ----------------------------------------------------------------------------

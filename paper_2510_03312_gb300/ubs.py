@@ -30,6 +30,7 @@ UBS_ROT_EXP = 5
 UBS_FLAG_TIGHT_CUT = 1
 UBS_FLAG_COUNT_PAIRS = 2
 UBS_FLAG_ACCUMULATE_GRADS = 4
+UBS_FLAG_PERSISTENT = 8
 UBS_ACT_IDENTITY = 0
 UBS_ACT_SIGMOID = 1
 UBS_ACT_EXP = 2

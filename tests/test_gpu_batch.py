@@ -106,7 +106,35 @@ def test_device_autotune_returns_a_valid_plan():
     plan = A.tune(wl.scenes, wl.views, wl.cfg, meas, tiles=((16, 16), (32, 32)),
                   schedules={k: A.SCHEDULES[k] for k in ("one_launch", "per_view")})
     assert plan.tile in ((16, 16), (32, 32)) and plan.ms > 0
-    assert len(plan.table) == 4
+    assert len(plan.table) == 4 * len(A.FORMS)
+
+
+@pytest.mark.parametrize("tile", A.TILES)
+@pytest.mark.parametrize("graph", [False, True])
+def test_persistent_blend_matches_the_grid(tile, graph):
+    """The persistent launch form of both blend kernels gives the grid
+    form's images bit for bit and the same gradients (up to float summation
+    order), on three steps in a row (its tile counters reset themselves),
+    eagerly and replayed from a captured graph."""
+    wl, ds = _jobs()
+    cfg = replace(wl.cfg, tile_w=tile[0], tile_h=tile[1])
+    per_view = _dl_per_view(wl.views)
+    ref_img, ref_g = _reference(ds, wl.views, cfg, per_view)
+    b = raster.Batch(ds, wl.views, replace(cfg, persistent=True), A.one_launch(wl.scenes, wl.views))
+    b.size()
+    dls = _batch_dls(b, per_view)
+    graph_obj = b.capture(dls) if graph else None
+    for step in range(3):
+        if graph:
+            graph_obj.replay()
+        else:
+            b.step(dls)
+        torch.cuda.synchronize()
+        assert all(st.status == 0 for st in b.status())
+        for i in range(len(wl.views)):
+            assert torch.equal(b.image(i), ref_img[i]), f"step {step}: view {i} differs"
+        for s, (x, y) in enumerate(zip(b.grads, ref_g)):
+            assert _close(x, y), f"step {step}, scene {s}: {float((x - y).abs().max()):.3e}"
 
 
 def test_dense_lists_over_many_tiles_match_views_alone():
@@ -138,3 +166,12 @@ def test_dense_lists_over_many_tiles_match_views_alone():
         g_sum += r1.backward(per_view[i].reshape(-1))[0]
         del r1
     assert _close(g, g_sum)
+    # the persistent form takes the same longest-first order from its counter
+    rp = raster.Rasterizer(ds, views, replace(cfg, persistent=True))
+    rp.forward(check=True)
+    for _ in range(2):
+        imgp = rp.forward(check=False)
+        gp = rp.backward(torch.cat([d.reshape(-1) for d in per_view]))[0]
+        torch.cuda.synchronize()
+        assert torch.equal(imgp, r.image)
+        assert _close(gp, g)
