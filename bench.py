@@ -424,6 +424,7 @@ def bench_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_batched and world == 1:
         out["batched"] = bench_batched(dev, pk, n_sm)
+        out["deep_tile"] = bench_deep_tile(dev)
         out["forward_only"] = bench_small_forward(dev)
     if dist:
         dist.destroy_process_group()
@@ -687,6 +688,52 @@ def batched_rooflines(ds, wl, dev, pk, n_sm, steps, warmup):
     return steps_roof, path, batch_pb, view_pb, pairs, visited
 
 
+def bench_deep_tile(dev, steps=5, warmup=2):
+    """The deep-tile workload (a dense cluster of 60K faint primitives inside
+    a few tiles, in front of a 300K-primitive sparse view, 1600x1060): one
+    fwd+bwd step with the tile lists blended whole (grid form) and split into
+    segments of 2048 entries merged with the over operator (split form)."""
+    import torch
+
+    from dataclasses import replace
+
+    from paper_2510_03312_gb300 import raster
+    from paper_2510_03312_gb300 import scenes as S
+
+    wl = S.workload_deep_tile()
+    ds = [raster.DeviceScene.from_scene(sc, device=dev) for sc in wl.scenes]
+    mp = sum(v.width * v.height for v in wl.views) / 1e6
+    out = {"workload": wl.name, "primitives": wl.scenes[0].P}
+    names = ["preprocess", "bin_sort", "render_fwd", "render_bwd_blend", "render_bwd_params"]
+    stream = torch.cuda.current_stream()
+    for form, cfg in (("grid", wl.cfg), ("split", replace(wl.cfg, split_lists=True))):
+        r = raster.Rasterizer(ds, wl.views, cfg, device=dev)
+        img = r.forward(check=True)
+        if form == "grid":
+            counts = r.export(5).cpu().numpy().view(np.uint32).astype(np.int64)
+            out["longest_list"] = int(np.diff(counts).max())
+        dL = torch.full_like(img, 1e-6)
+        calls = [r.preprocess, r.bin_sort, r.render_fwd, lambda: r.render_bwd_blend(dL), r.render_bwd_params]
+        rows = []
+        for i in range(warmup + steps):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            evs[0].record(stream)
+            for k, c in enumerate(calls):
+                c()
+                evs[k + 1].record(stream)
+            if i >= warmup:
+                rows.append(evs)
+        torch.cuda.synchronize()
+        stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(5)] for e in rows]).mean(0)
+        ms = float(stage.sum())
+        out[form] = {"ms_per_step": round(ms, 4), "MP_per_s": round(mp / (ms / 1e3), 2),
+                     "stage_ms": {n: round(float(m), 4) for n, m in zip(names, stage)}}
+        del r
+        torch.cuda.empty_cache()
+    out["speedup_split"] = round(out["grid"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
+    return out
+
+
 def bench_batched(dev, pk, n_sm, steps=5, warmup=2):
     """Batches of views, forward+backward per step:
       view-dependent N=6, 500K primitives, 16 x 1280x720;
@@ -731,14 +778,14 @@ def bench_batched(dev, pk, n_sm, steps=5, warmup=2):
         plan = A.tune(wl.scenes, wl.views, wl.cfg, A.device_measure(ds, wl.views, wl.cfg, device=dev))
         t_tune = time.perf_counter() - t0
         from dataclasses import replace
-        cfg = replace(wl.cfg, tile_w=plan.tile[0], tile_h=plan.tile[1], persistent=plan.persistent)
+        cfg = plan.config(wl.cfg)
         b = raster.Batch(ds, wl.views, cfg, plan.groups, device=dev)
         b.size()
         dls = b.dL_like(1e-6)
         g = b.capture(dls)
         out["batched"] = entry(time_calls(g.replay, steps, warmup))
         out["batched"].update({"tile": f"{plan.tile[0]}x{plan.tile[1]}", "schedule": plan.schedule,
-                               "blend_launch": "persistent" if plan.persistent else "grid",
+                               "blend_launch": plan.form,
                                "launches": len(plan.groups), "captured_graph": True})
         out["autotune"] = {"seconds": round(t_tune, 1), "candidates_ms": plan.table}
         out["speedup_batched"] = round(out["per_view"]["ms_per_step"] / out["batched"]["ms_per_step"], 3)

@@ -89,9 +89,18 @@ enum {
                                    gradients to the ubs_scene_grad buffers instead of
                                    overwriting them: a scene rendered by several problems
                                    (launches) gets the sum over all of its views */
-  UBS_FLAG_PERSISTENT = 8 /* the blend kernels run as persistent grids (one CTA per resident
-                             slot) that take tiles or 8x8 blocks from a counter in the same order,
-                             instead of one CTA per tile or block; the results are the same */
+  UBS_FLAG_PERSISTENT = 8, /* the blend kernels run as persistent grids (one CTA per resident
+                              slot) that take tiles or 8x8 blocks from a counter in the same order,
+                              instead of one CTA per tile or block; the results are the same */
+  UBS_FLAG_SPLIT_LISTS = 16 /* tile lists longer than 2048 entries are split into segments of 2048
+                               blended by separate CTAs and merged front to back with the over
+                               operator (C = C_1 + T_1 C_2, T = T_1 T_2), walking a segment again
+                               for the pixels whose transmittance falls below T_min inside it; the
+                               backward walks the segments in parallel from each segment's end.
+                               Images and gradients agree with the unsplit form up to float
+                               rounding.  Takes precedence over UBS_FLAG_PERSISTENT; ignored by
+                               the UBS_FLAG_COUNT_PAIRS variant.  Needs a larger workspace (see
+                               ubs_workspace_size) */
 };
 
 /* One primitive set (Sec. 4.1-4.3).  Structure of arrays: every block below

@@ -2,8 +2,8 @@
 
 A plan is a tile shape for the blend (one of the shapes the kernels are
 built for), a launch form of the blend kernels (one CTA per tile or 8x8
-block, or a persistent grid that takes them from a counter) and a
-schedule: a partition of the views into launches, each launch one problem
+block, a persistent grid that takes them from a counter, or the grid with
+long lists split into segments) and a schedule: a partition of the views into launches, each launch one problem
 over the scenes its views use.  Candidates are timed on
 the device by replaying a captured CUDA graph of the whole forward+backward
 step, and the fastest is kept, cached under a signature of the batch's
@@ -24,7 +24,7 @@ import os
 from dataclasses import dataclass, field
 
 TILES = ((8, 8), (16, 16), (16, 32), (32, 32))
-FORMS = (False, True)  # blend launch form: grid, persistent
+FORMS = ("grid", "persistent", "split")  # launch forms of the blend kernels
 MAX_VIEWS = 256  # views per problem accepted by the C-ABI
 
 
@@ -77,7 +77,7 @@ def signature(scenes, views, cfg, tiles, schedules, forms=FORMS) -> str:
                 float(cfg.near), bool(cfg.tight_cut)],
         "tiles": [list(t) for t in tiles],
         "schedules": sorted(schedules),
-        "forms": [bool(f) for f in forms],
+        "forms": [str(f) for f in forms],
     }
     return hashlib.sha256(json.dumps(d, sort_keys=True).encode()).hexdigest()[:24]
 
@@ -88,17 +88,29 @@ class Plan:
     schedule: str
     groups: list
     ms: float
-    table: dict = field(default_factory=dict)  # "WxH/schedule[/persistent]" -> ms
-    persistent: bool = False
+    table: dict = field(default_factory=dict)  # "WxH/schedule/form" -> ms
+    form: str = "grid"
+
+    def config(self, cfg):
+        """``cfg`` with this plan's tile shape and launch form."""
+        from dataclasses import replace
+        return replace(cfg, tile_w=int(self.tile[0]), tile_h=int(self.tile[1]), **form_fields(self.form))
 
     def to_json(self):
         return {"tile": list(self.tile), "schedule": self.schedule, "groups": self.groups, "ms": self.ms,
-                "table": self.table, "persistent": self.persistent}
+                "table": self.table, "form": self.form}
 
     @classmethod
     def from_json(cls, d):
         return cls(tuple(d["tile"]), d["schedule"], [list(g) for g in d["groups"]], float(d["ms"]),
-                   dict(d.get("table", {})), bool(d.get("persistent", False)))
+                   dict(d.get("table", {})), str(d.get("form", "grid")))
+
+
+def form_fields(form: str) -> dict:
+    """RasterConfig fields of a launch form."""
+    if form not in FORMS:
+        raise ValueError(f"unknown launch form {form!r}")
+    return {"persistent": form == "persistent", "split_lists": form == "split"}
 
 
 class PlanCache:
@@ -126,8 +138,8 @@ class PlanCache:
 def tune(scenes, views, cfg, measure, tiles=TILES, schedules=None, cache: PlanCache | None = None,
          forms=FORMS) -> Plan:
     """Times every (tile, schedule, launch form) candidate with
-    ``measure(tile, groups, persistent)`` (milliseconds per forward+backward
-    step) and returns the fastest plan.  ``scenes`` need ``N``,
+    ``measure(tile, groups, form)`` (milliseconds per forward+backward step)
+    and returns the fastest plan.  ``scenes`` need ``N``,
     ``rot_mode`` and ``P``; ``views`` need ``width``, ``height`` and
     ``scene_id``.  Ties go to the earlier candidate."""
     schedules = SCHEDULES if schedules is None else schedules
@@ -140,11 +152,11 @@ def tune(scenes, views, cfg, measure, tiles=TILES, schedules=None, cache: PlanCa
     for tile in tiles:
         for name, make in schedules.items():
             groups = make(scenes, views)
-            for persistent in forms:
-                ms = float(measure(tuple(tile), groups, bool(persistent)))
-                table[f"{tile[0]}x{tile[1]}/{name}" + ("/persistent" if persistent else "")] = round(ms, 4)
+            for form in forms:
+                ms = float(measure(tuple(tile), groups, form))
+                table[f"{tile[0]}x{tile[1]}/{name}/{form}"] = round(ms, 4)
                 if best is None or ms < best.ms:
-                    best = Plan(tuple(tile), name, groups, ms, persistent=bool(persistent))
+                    best = Plan(tuple(tile), name, groups, ms, form=form)
     if best is None:
         raise ValueError("no candidates")
     best.table = table
@@ -165,8 +177,8 @@ def device_measure(scenes, views, cfg, device="cuda", steps=3, warmup=1):
 
     from .raster import Batch
 
-    def measure(tile, groups, persistent=False):
-        c = replace(cfg, tile_w=int(tile[0]), tile_h=int(tile[1]), persistent=bool(persistent))
+    def measure(tile, groups, form="grid"):
+        c = replace(cfg, tile_w=int(tile[0]), tile_h=int(tile[1]), **form_fields(form))
         b = Batch(scenes, views, c, groups, device=device)
         b.size()
         dls = b.dL_like(1e-6)

@@ -129,6 +129,19 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.Tfin = take((size_t)L.NPIX * 4);
   L.last = take((size_t)L.NPIX * 4);
   L.pairs = take((size_t)L.NPIX * 8);  // pairs with r < 1, then visited entries
+  if (c.flags & kFlagSplit) {
+    // a split tile holds more than kSegLen instances, and its segments number
+    // at most its instances / kSegLen + 1: bounds from the capacity
+    L.seg_max_split = L.cap / kSegLen + 1;
+    L.seg_max_extra = L.cap / kSegLen + 1;
+    L.seg_slots = 2 * (L.cap / kSegLen) + 2;
+    L.split_list = take((size_t)L.seg_max_split * 16);
+    L.tile_slot = take((size_t)L.NT * 4);
+    L.seg_buf = take((size_t)L.seg_slots * (size_t)c.tile_w * (size_t)c.tile_h * 32);
+    L.slot_owner = take((size_t)L.seg_slots * 4);
+    L.ext_owner = take((size_t)L.seg_max_extra * 4);
+    L.split_term = take((size_t)L.seg_max_split * 4);
+  }
   L.total = o;
   return UBS_OK;
 }

@@ -101,8 +101,23 @@ struct Layout {
   size_t act_list;   // per scene (at the sum of the earlier scenes' P): primitives visible in some view
   size_t act_count;  // their number per scene [kMaxScenes]
   size_t Tfin, last, pairs;
+  // long tile lists split across CTAs (UBS_FLAG_SPLIT_LISTS): the split
+  // tiles [seg_max_split] x (tile, first slot, segments, first extra
+  // segment), each tile's first slot or ~0 [NT], and per (slot, pixel of
+  // the tile) 8 floats of segment state [seg_slots][tile pixels][8]
+  size_t split_list, tile_slot, seg_buf;
+  size_t slot_owner;  // split tile of each slot [seg_slots]
+  size_t ext_owner;   // split tile of each extra segment [seg_max_extra]
+  size_t split_term;  // per split tile: the first segment after which every pixel had ended [seg_max_split]
+  uint32_t seg_max_split, seg_max_extra, seg_slots;
   size_t total;
 };
+
+// Tiles whose lists are longer than kSegLen entries are split into segments
+// of kSegLen entries (a multiple of every blend batch size) when
+// UBS_FLAG_SPLIT_LISTS is set.
+constexpr uint32_t kSegLen = 2048;
+constexpr uint32_t kFlagSplit = 16;
 
 // float record of one (view, primitive) for the blend kernels: 3 x float4
 //   [mu'_x hi, mu'_y hi, mu'_x lo, mu'_y lo]

@@ -266,14 +266,36 @@ struct FwdArgs {
   const uint32_t* __restrict__ tile_order;
   uint32_t n_tiles, cap;
   uint32_t* queue;  // persistent form: [next tile, finished CTAs], zero between launches
+  // split lists (UBS_FLAG_SPLIT_LISTS): the plan made by split_plan_kernel
+  const uint4* split_list;
+  const uint32_t* tile_split;  // split index of each tile, or ~0
+  const uint32_t* slot_owner;  // split index of each slot
+  const uint32_t* ext_owner;   // split index of each extra segment
+  uint32_t* split_term;        // per split tile: first segment after which every pixel had ended
+  float4* seg_buf;
+  uint32_t max_extra;
 };
 
-// One tile g, by the whole CTA (every thread calls it).
-template <int TW, int TH, bool COUNT>
-__device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<TW, TH>& sm) {
+// One tile g, by the whole CTA (every thread calls it).  With SPLIT it
+// walks only the list positions [wbeg, wend) of the tile and, when `slot`
+// is given, writes each pixel's state there (colour, T, last contributor
+// and whether the pixel terminated) instead of the image: the part of one
+// segment of a split list.
+// A segment k > 0 that learns (through `term`) that an earlier segment ended
+// every pixel of the tile stops: no pixel's result can use it.  A segment
+// whose walk ends every pixel records its index there.
+template <int TW, int TH, bool COUNT, bool SPLIT = false>
+__device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<TW, TH>& sm, uint32_t wbeg = 0,
+                                         uint32_t wend = 0xffffffffu, float4* slot = nullptr,
+                                         bool resume = false, uint32_t* term = nullptr, uint32_t seg = 0) {
   constexpr int NT = FwdSmem<TW, TH>::NT, BS = FwdSmem<TW, TH>::BS;
   const CfgDev& cfg = A.cfg;
-  const uint32_t start = A.tstart[g], end = A.tstart[g + 1];  // loaded while warp 0 finds the view
+  uint32_t start = A.tstart[g], end = A.tstart[g + 1];  // loaded while warp 0 finds the view
+  const uint32_t list0 = start;  // positions are numbered from the tile list's first entry
+  if constexpr (SPLIT) {
+    start = min(end, list0 + wbeg);
+    end = min(end, list0 + min(wend, 0xffffffffu - list0));
+  }
   if (threadIdx.x < 32) {
     const int vi = find_view_warp(A.views, A.V, g);
     if (threadIdx.x == 0) sm.v = vi;
@@ -296,8 +318,30 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
   float2 T = one, C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0;
   uint32_t last0 = 0, last1 = 0, np0 = 0, np1 = 0, nv = 0;
   bool done0 = !in0, done1 = !in1;
+  bool need0 = true, need1 = true;
+  if constexpr (SPLIT) {
+    if (resume) {  // a pixel whose walk ends in this segment resumes from its T and last contributor
+      const float4 a0 = slot[2 * (ly * TW + lx)], a1 = slot[2 * (ly * TW + lx) + 1];
+      const float4 b0 = slot[2 * ((ly + 4) * TW + lx)], b1 = slot[2 * ((ly + 4) * TW + lx) + 1];
+      need0 = __float_as_uint(a1.y) != 0u;
+      need1 = __float_as_uint(b1.y) != 0u;
+      T = make_float2(a0.w, b0.w);
+      last0 = __float_as_uint(a1.x);
+      last1 = __float_as_uint(b1.x);
+      done0 = done0 || !need0;
+      done1 = done1 || !need1;
+    }
+  }
   for (uint32_t base = start; base < end; base += BS) {
+    if constexpr (SPLIT) {
+      // read by one thread before the barrier, by all after it; rewritten only
+      // after this batch's staging barrier, which every reader has passed
+      if (term && seg > 0 && threadIdx.x == 0) sm.next = *(volatile const uint32_t*)term < seg ? 1u : 0u;
+    }
     if (__syncthreads_count(done0 && done1) == NT) break;
+    if constexpr (SPLIT) {
+      if (term && seg > 0 && sm.next) return;  // an earlier segment ended every pixel of the tile
+    }
     const uint32_t idx = base + threadIdx.x;
     if (threadIdx.x < BS && idx < end) {
       Staged st;
@@ -311,7 +355,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
     // the counting variant walks every entry, to count every pair with r < 1,
     // and also counts the entries the cull would have kept (visited)
     const int cnt = warp_cull_list2(sm.bb, sm.st, sm.rc, n, COUNT, wx0, wx1, wy0, wy1, list);
-    const uint32_t rel = base - start;
+    const uint32_t rel = base - list0;
     // one entry for both pixels; branch-free: a pair that is skipped (or
     // stops its pixel) adds c * 0 and keeps T, which leaves C and T exactly
     auto blend = [&](int j) {
@@ -354,6 +398,22 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
       if (i + 1 < cnt) blend(list[i + 1]);
     }
   }
+  if constexpr (SPLIT) {
+    if (term && __syncthreads_count(done0 && done1) == NT && threadIdx.x == 0) atomicMin(term, seg);
+    if (slot) {  // one segment's state of the lane's two pixels (only the resumed ones when resuming)
+      float4* s0 = slot + 2 * (ly * TW + lx);
+      float4* s1 = slot + 2 * ((ly + 4) * TW + lx);
+      if (need0) {
+        s0[0] = make_float4(C0.x, C1.x, C2.x, T.x);
+        s0[1] = make_float4(__uint_as_float(last0), __uint_as_float(done0 ? 1u : 0u), 0.0f, 0.0f);
+      }
+      if (need1) {
+        s1[0] = make_float4(C0.y, C1.y, C2.y, T.y);
+        s1[1] = make_float4(__uint_as_float(last1), __uint_as_float(done1 ? 1u : 0u), 0.0f, 0.0f);
+      }
+      return;
+    }
+  }
   const size_t plane = (size_t)v.W * v.H;
   float* img = A.image + (size_t)v.pix_off * 3;
   if (in0) {
@@ -383,16 +443,83 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
 }
 
 // The grid form: one CTA per tile, in bin_sort's tile order where the lists
-// are dense.
-template <int TW, int TH, bool COUNT>
+// are dense.  With SPLIT a split tile's own CTA walks its first segment, and
+// A.max_extra more CTAs after the tiles' walk the later segments (those that
+// split_plan_kernel did not assign exit): started after the tiles, they can
+// find their tile already ended by its first segment, as dense tiles are.
+template <int TW, int TH, bool COUNT, bool SPLIT>
 __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW * TH / 2) : 16))
     render_fwd_kernel(FwdArgs A) {
   wait_prior_grid();
   __shared__ FwdSmem<TW, TH> sm;
   if (A.hdr->status != 0) return;
-  const uint32_t g =
-      A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[blockIdx.x] : blockIdx.x;
-  fwd_tile<TW, TH, COUNT>(A, g, sm);
+  uint32_t t = blockIdx.x;
+  if constexpr (SPLIT) {
+    constexpr int TP = TW * TH;  // pixels per tile: the float4 pairs of a slot
+    if (t >= A.n_tiles) {
+      // extra segment e: the split tile whose extra segments [w, w + m - 1) hold it
+      const uint32_t e = t - A.n_tiles;
+      if (e >= A.hdr->ctr[6]) return;
+      const uint32_t i = A.ext_owner[e];
+      const uint4 sp = A.split_list[i];
+      const uint32_t k = e - sp.w + 1;
+      fwd_tile<TW, TH, COUNT, true>(A, sp.x, sm, k * kSegLen, (k + 1) * kSegLen,
+                                    A.seg_buf + (size_t)(sp.y + k) * TP * 2, false, A.split_term + i, k);
+      return;
+    }
+    const uint32_t g = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[t] : t;
+    const uint32_t i = A.tile_split[g];
+    if (i != 0xffffffffu)
+      fwd_tile<TW, TH, COUNT, true>(A, g, sm, 0, kSegLen, A.seg_buf + (size_t)A.split_list[i].y * TP * 2, false,
+                                    A.split_term + i, 0);
+    else
+      fwd_tile<TW, TH, COUNT, true>(A, g, sm);
+  } else {
+    const uint32_t g = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[t] : t;
+    fwd_tile<TW, TH, COUNT>(A, g, sm);
+  }
+}
+
+__device__ __forceinline__ void set_status_dev(const Header* h, uint32_t s) {
+  atomicCAS(const_cast<uint32_t*>(&h->status), 0u, s);
+}
+
+// The plan of split lists: every tile whose list holds more than kSegLen
+// entries gets a split index i, m = ceil(n / kSegLen) consecutive slots of
+// segment state and m - 1 extra segments (CTAs of the split grids), in the
+// order the atomics hand them out; tile_split, slot_owner and ext_owner map
+// tiles, slots and extra segments to i.  The counters (header ctr[4..6]) are
+// zeroed before the launch.
+__global__ void __launch_bounds__(256) split_plan_kernel(const uint32_t* __restrict__ tstart, uint32_t NT,
+                                                         uint4* __restrict__ split_list,
+                                                         uint32_t* __restrict__ tile_split,
+                                                         uint32_t* __restrict__ slot_owner,
+                                                         uint32_t* __restrict__ ext_owner,
+                                                         uint32_t* __restrict__ split_term, uint32_t max_split,
+                                                         uint32_t max_slots, uint32_t max_extra, Header* hdr) {
+  wait_prior_grid();
+  if (hdr->status != 0) return;
+  for (uint32_t g = blockIdx.x * 256 + threadIdx.x; g < NT; g += gridDim.x * 256) {
+    const uint32_t n = tstart[g + 1] - tstart[g];
+    uint32_t split = 0xffffffffu;
+    if (n > kSegLen) {
+      const uint32_t m = (n + kSegLen - 1) / kSegLen;
+      const uint32_t i = atomicAdd(&hdr->ctr[4], 1u);
+      const uint32_t b = atomicAdd(&hdr->ctr[5], m);
+      const uint32_t e = atomicAdd(&hdr->ctr[6], m - 1);
+      // within the bounds by construction (at most the capacity's instances)
+      if (i < max_split && b + m <= max_slots && e + m - 1 <= max_extra) {
+        split_list[i] = make_uint4(g, b, m, e);
+        split_term[i] = 0xffffffffu;
+        for (uint32_t k = 0; k < m; ++k) slot_owner[b + k] = i;
+        for (uint32_t k = 0; k + 1 < m; ++k) ext_owner[e + k] = i;
+        split = i;
+      } else {
+        set_status_dev(hdr, kDevInternal);
+      }
+    }
+    tile_split[g] = split;
+  }
 }
 
 // The persistent form: as many CTAs as fit on the GPU at once, each taking
@@ -416,6 +543,137 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
   if (threadIdx.x == 0 && atomicAdd(A.queue + 1, 1u) == gridDim.x - 1) {
     A.queue[0] = 0;  // every CTA has taken its last tile
     A.queue[1] = 0;
+  }
+}
+
+// The merge of a split tile's segments takes three kernels.  Every
+// segment but the first was walked from T = 1 (and stopped only where its
+// own T fell below T_min, which the true T, no larger, would have done
+// sooner).  Front to back, the over operator joins them exactly
+// (C += T C_k, T *= T_k) as long as the pixel's true transmittance stays at
+// or above T_min through segment k; the first segment k* where it would not
+// (the local walk stopped, or T T_k < T_min) is where the pixel's walk ends,
+// and that segment is walked again from the pixel's true T.
+//
+// Pass 1 (one CTA per split tile, a thread per pixel): the over operator up
+// to k*.  Slot k < k* gets the colour segment k adds (absolute) and T at its
+// end; slot k* gets the pixel's T and last contributor at its start and a
+// "walk again" mark; slot 0 records k* (m when the walk never ends early)
+// and the last contributor.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) split_join_kernel(FwdArgs A) {
+  wait_prior_grid();
+  constexpr int TP = TW * TH;
+  if (A.hdr->status != 0) return;
+  if (blockIdx.x >= A.hdr->ctr[4]) return;
+  const uint4 sp = A.split_list[blockIdx.x];
+  const uint32_t m = sp.z;
+  float4* my = A.seg_buf + (size_t)sp.y * TP * 2 + 2 * threadIdx.x;  // slot k: my[2 k TP], my[2 k TP + 1]
+  const CfgDev& cfg = A.cfg;
+  const float4 s0 = my[0], s1 = my[1];
+  float T = s0.w;
+  uint32_t last = __float_as_uint(s1.x);
+  bool done = __float_as_uint(s1.y) != 0u;  // ended in the first segment (exact), or outside the image
+  uint32_t kstar = m;
+  my[1] = make_float4(s1.x, 0.0f, 0.0f, 0.0f);
+  for (uint32_t k = 1; k < m; ++k) {
+    float4* mk = my + (size_t)2 * k * TP;
+    const float4 a0 = mk[0], a1 = mk[1];
+    if (kstar < m || done) {  // after the walk ended: the segment adds nothing
+      mk[0] = make_float4(0.0f, 0.0f, 0.0f, T);
+      mk[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      continue;
+    }
+    const float Tk = __fmul_rn(T, a0.w);
+    if (__float_as_uint(a1.y) != 0u || Tk < cfg.tmin) {
+      kstar = k;
+      mk[0] = make_float4(0.0f, 0.0f, 0.0f, T);
+      mk[1] = make_float4(__uint_as_float(last), __uint_as_float(1u), 0.0f, 0.0f);
+      continue;
+    }
+    mk[0] = make_float4(__fmul_rn(T, a0.x), __fmul_rn(T, a0.y), __fmul_rn(T, a0.z), Tk);
+    mk[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    T = Tk;
+    const uint32_t lk = __float_as_uint(a1.x);
+    last = lk ? lk : last;
+  }
+  my[1] = make_float4(__uint_as_float(last), 0.0f, __uint_as_float(kstar), 0.0f);
+}
+
+// Pass 2 (one CTA per slot): the segments that pass 1 marked are walked
+// again, with the forward blend's own tile walk, only for the marked pixels,
+// from their true T (colour from zero); all the segments run at once.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW * TH / 2) : 16))
+    split_resume_kernel(FwdArgs A) {
+  wait_prior_grid();
+  constexpr int TP = TW * TH;
+  __shared__ FwdSmem<TW, TH> sm;
+  if (A.hdr->status != 0) return;
+  const uint32_t s = blockIdx.x;
+  if (s >= A.hdr->ctr[5]) return;  // unused
+  const uint4 sp = A.split_list[A.slot_owner[s]];
+  const uint32_t k = s - sp.y;
+  if (k == 0) return;  // the first segment is exact
+  fwd_tile<TW, TH, false, true>(A, sp.x, sm, k * kSegLen, (k + 1) * kSegLen, A.seg_buf + (size_t)s * TP * 2, true);
+}
+
+// Pass 3 (one CTA per split tile, a thread per pixel): the pixel's colour,
+// final T and last contributor, written to the image; and, for the
+// backward, each segment's T at its end and the colour behind it
+// (everything after it and the background), normalised by that T.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) split_finish_kernel(FwdArgs A) {
+  wait_prior_grid();
+  constexpr int TP = TW * TH;
+  __shared__ int s_v;
+  if (A.hdr->status != 0) return;
+  if (blockIdx.x >= A.hdr->ctr[4]) return;
+  const uint4 sp = A.split_list[blockIdx.x];
+  const uint32_t g = sp.x, m = sp.z;
+  if (threadIdx.x < 32) {
+    const int vi = find_view_warp(A.views, A.V, g);
+    if (threadIdx.x == 0) s_v = vi;
+  }
+  __syncthreads();
+  const ViewDev& v = A.views[s_v];
+  const CfgDev& cfg = A.cfg;
+  float4* my = A.seg_buf + (size_t)sp.y * TP * 2 + 2 * threadIdx.x;
+  const float4 h1 = my[1];
+  uint32_t last = __float_as_uint(h1.x);
+  const uint32_t kstar = __float_as_uint(h1.z);
+  float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
+  const uint32_t kend = kstar < m ? kstar : m - 1;  // the segment the walk ends in
+  for (uint32_t k = 0; k <= kend; ++k) {
+    const float4 a0 = my[(size_t)2 * k * TP];
+    C0 += a0.x;
+    C1 += a0.y;
+    C2 += a0.z;
+    T = a0.w;
+  }
+  if (kstar < m) last = __float_as_uint(my[(size_t)2 * kstar * TP + 1].x);
+  const uint32_t lt = g - v.tile_off;
+  const int tx = lt % v.tiles_x, ty = lt / v.tiles_x;
+  const int x = tx * TW + (int)(threadIdx.x % TW), y = ty * TH + (int)(threadIdx.x / TW);
+  if (x < v.W && y < v.H) {
+    const size_t plane = (size_t)v.W * v.H, pix = (size_t)y * v.W + x;
+    float* img = A.image + (size_t)v.pix_off * 3;
+    img[pix] = fmaf(T, cfg.bg[0], C0);
+    img[plane + pix] = fmaf(T, cfg.bg[1], C1);
+    img[2 * plane + pix] = fmaf(T, cfg.bg[2], C2);
+    A.Tfin[v.pix_off + pix] = T;
+    A.lastc[v.pix_off + pix] = last;
+  }
+  float b0 = T * cfg.bg[0], b1 = T * cfg.bg[1], b2 = T * cfg.bg[2];
+  for (int k = (int)m - 1; k >= 0; --k) {
+    float4* mk = my + (size_t)2 * k * TP;
+    float4 a0 = make_float4(0.0f, 0.0f, 0.0f, T);  // after the walk ended: nothing added, T final
+    if ((uint32_t)k <= kend) a0 = mk[0];
+    const float inv = a0.w > 0.0f ? 1.0f / a0.w : 0.0f;
+    mk[1] = make_float4(b0 * inv, b1 * inv, b2 * inv, a0.w);
+    b0 += a0.x;
+    b1 += a0.y;
+    b2 += a0.z;
   }
 }
 
@@ -502,11 +760,21 @@ struct BwdArgs {
   const uint32_t* __restrict__ tile_order;
   uint32_t n_tiles, cap;
   uint32_t* queue;  // persistent form: [next block, finished CTAs], zero between launches
+  // split lists: the forward's plan and segment state
+  const uint4* split_list;
+  const uint32_t* tile_split;
+  const uint32_t* ext_owner;
+  const float4* seg_buf;
+  uint32_t max_extra;
 };
 
-// One 8x8 block wb of tile g, by one warp.
-template <int TW, int TH>
-__device__ __forceinline__ void bwd_block(const BwdArgs& A, uint32_t g, int wb, BwdSmem& sm) {
+// One 8x8 block wb of tile g, by one warp.  With SPLIT and a slot, only the
+// list positions [wbeg, wend) of one segment are walked, from the
+// transmittance and colour behind at the segment's end that the forward's
+// merge left in the slot.
+template <int TW, int TH, bool SPLIT = false>
+__device__ __forceinline__ void bwd_block(const BwdArgs& A, uint32_t g, int wb, BwdSmem& sm, uint32_t wbeg = 0,
+                                          uint32_t wend = 0xffffffffu, const float4* slot = nullptr) {
   constexpr int WB = BwdSmem::WB;
   constexpr int WPR = TW / 8;  // blocks per row of the tile
   const CfgDev& cfg = A.cfg;
@@ -549,15 +817,29 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& A, uint32_t g, int wb, 
       last1 = A.lastc[v.pix_off + pix];
     }
   }
-  const uint32_t wlast = __reduce_max_sync(kFull, max(last0, last1));
+  if constexpr (SPLIT) {
+    if (slot) {  // the segment's end: T and the normalised colour behind it
+      const float4 s0 = slot[2 * (ly * TW + lx) + 1], s1 = slot[2 * ((ly + 4) * TW + lx) + 1];
+      T = make_float2(s0.w, s1.w);
+      B0 = make_float2(s0.x, s1.x);
+      B1 = make_float2(s0.y, s1.y);
+      B2 = make_float2(s0.z, s1.z);
+    }
+  }
+  uint32_t wlast = __reduce_max_sync(kFull, max(last0, last1));
+  if constexpr (SPLIT) {
+    wlast = min(wlast, wend);
+    if (wlast <= wbeg) return;
+  }
   if (wlast == 0) return;
   const float ox = (float)(tx * TW), oy = (float)(ty * TH);
   const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 7.0f;
   const float lg2_amin = lg2_approx(cfg.amin);
   const float2 one = make_float2(1.0f, 1.0f), neg1 = make_float2(-1.0f, -1.0f);
   const int wslot = writer_of(lane);
-  for (int hi = (int)wlast; hi > 0; hi -= WB) {
-    const int lo = hi - WB > 0 ? hi - WB : 0;
+  const int wfirst = SPLIT ? (int)wbeg : 0;
+  for (int hi = (int)wlast; hi > wfirst; hi -= WB) {
+    const int lo = hi - WB > wfirst ? hi - WB : wfirst;
     const int n = hi - lo;
     bool listed = false;
     if (lane < n) {
@@ -648,22 +930,47 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& A, uint32_t g, int wb, 
   }
 }
 
-// The grid form: one single-warp CTA per 8x8 block.
-template <int TW, int TH>
+// The grid form: one single-warp CTA per 8x8 block.  With SPLIT the grid
+// first holds the blocks of A.max_extra extra segments (those the plan did
+// not assign exit), and a split tile's own blocks walk its first segment.
+template <int TW, int TH, bool SPLIT>
 __global__ void __launch_bounds__(32, 32)  // 64 registers: 32 one-warp CTAs per SM
     render_bwd_kernel(BwdArgs A) {
   wait_prior_grid();
   constexpr int BPT = TW * TH / 64;  // 8x8 blocks per tile
   __shared__ BwdSmem sm;
   if (A.hdr->status != 0) return;
-  const uint32_t t = blockIdx.x / BPT;
-  const uint32_t g = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[t] : t;
-  bwd_block<TW, TH>(A, g, blockIdx.x % BPT, sm);
+  uint32_t t = blockIdx.x / BPT;
+  const int wb = blockIdx.x % BPT;
+  if constexpr (SPLIT) {
+    constexpr int TP = TW * TH;
+    if (t < A.max_extra) {
+      if (t >= A.hdr->ctr[6]) return;
+      const uint4 sp = A.split_list[A.ext_owner[t]];
+      const uint32_t k = t - sp.w + 1;
+      bwd_block<TW, TH, true>(A, sp.x, wb, sm, k * kSegLen, (k + 1) * kSegLen,
+                              A.seg_buf + (size_t)(sp.y + k) * TP * 2);
+      return;
+    }
+    t -= A.max_extra;
+    const uint32_t g = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[t] : t;
+    const uint32_t i = A.tile_split[g];
+    if (i != 0xffffffffu)
+      bwd_block<TW, TH, true>(A, g, wb, sm, 0, kSegLen, A.seg_buf + (size_t)A.split_list[i].y * TP * 2);
+    else
+      bwd_block<TW, TH, true>(A, g, wb, sm);
+  } else {
+    const uint32_t g = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap) ? A.tile_order[t] : t;
+    bwd_block<TW, TH>(A, g, wb, sm);
+  }
 }
 
 // The persistent form: as many one-warp CTAs as fit on the GPU at once, each
-// taking the next 8x8 block (same order) from a counter until none is left;
-// the last CTA to finish resets the counters for the next launch.
+// taking the next tile (same order) from a counter and walking its 8x8
+// blocks in turn, until none is left (one counter update per tile, not per
+// block: a single counter updated once per block by thousands of warps
+// serialises); the last CTA to finish resets the counters for the next
+// launch.
 template <int TW, int TH>
 __global__ void __launch_bounds__(32, 32)
     render_bwd_persistent_kernel(BwdArgs A) {
@@ -672,15 +979,16 @@ __global__ void __launch_bounds__(32, 32)
   __shared__ BwdSmem sm;
   if (A.hdr->status != 0) return;
   const bool dense = A.tile_order && order_dense(A.hdr, A.n_tiles, A.cap);
-  const uint32_t n_blocks = A.n_tiles * BPT;
   for (;;) {
-    uint32_t b = 0;
-    if (threadIdx.x == 0) b = atomicAdd(A.queue, 1u);
-    b = __shfl_sync(kFull, b, 0);
-    if (b >= n_blocks) break;
-    const uint32_t t = b / BPT;
-    bwd_block<TW, TH>(A, dense ? A.tile_order[t] : t, b % BPT, sm);
-    __syncwarp();
+    uint32_t t = 0;
+    if (threadIdx.x == 0) t = atomicAdd(A.queue, 1u);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= A.n_tiles) break;
+    const uint32_t g = dense ? A.tile_order[t] : t;
+    for (int wb = 0; wb < BPT; ++wb) {
+      bwd_block<TW, TH>(A, g, wb, sm);
+      __syncwarp();
+    }
   }
   if (threadIdx.x == 0 && atomicAdd(A.queue + 1, 1u) == gridDim.x - 1) {
     A.queue[0] = 0;  // every CTA has taken its last block
@@ -729,7 +1037,30 @@ cudaError_t fwd_launch(const FwdArgs& args, const Layout& L, bool persistent, cu
       return launch_dependent(render_fwd_persistent_kernel<TW, TH, COUNT>, dim3(n < L.NT ? n : L.NT), dim3(NT), 0,
                               st, args);
   }
-  return launch_dependent(render_fwd_kernel<TW, TH, COUNT>, dim3(L.NT), dim3(NT), 0, st, args);
+  return launch_dependent(render_fwd_kernel<TW, TH, COUNT, false>, dim3(L.NT), dim3(NT), 0, st, args);
+}
+
+// Split lists: the plan (after zeroing its counters), the grid of extra
+// segments and tiles, and the merge of the split tiles.
+template <int TW, int TH>
+cudaError_t fwd_split(const FwdArgs& args, const Layout& L, char* ws, cudaStream_t st) {
+  constexpr int NT = TW * TH / 2;
+  Header* hdr = (Header*)(ws + L.header);
+  cudaError_t e = cudaMemsetAsync(&hdr->ctr[4], 0, 3 * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const uint32_t pb = (L.NT + 255) / 256;
+  e = launch_dependent(split_plan_kernel, dim3(pb < 1024 ? pb : 1024), dim3(256), 0, st,
+                       (const uint32_t*)(ws + L.tstart), L.NT, (uint4*)(ws + L.split_list),
+                       (uint32_t*)(ws + L.tile_slot), (uint32_t*)(ws + L.slot_owner), (uint32_t*)(ws + L.ext_owner),
+                       (uint32_t*)(ws + L.split_term), L.seg_max_split, L.seg_slots, L.seg_max_extra, hdr);
+  if (e != cudaSuccess) return e;
+  e = launch_dependent(render_fwd_kernel<TW, TH, false, true>, dim3(L.seg_max_extra + L.NT), dim3(NT), 0, st, args);
+  if (e != cudaSuccess) return e;
+  e = launch_dependent(split_join_kernel<TW, TH>, dim3(L.seg_max_split), dim3(TW * TH), 0, st, args);
+  if (e != cudaSuccess) return e;
+  e = launch_dependent(split_resume_kernel<TW, TH>, dim3(L.seg_slots), dim3(NT), 0, st, args);
+  if (e != cudaSuccess) return e;
+  return launch_dependent(split_finish_kernel<TW, TH>, dim3(L.seg_max_split), dim3(TW * TH), 0, st, args);
 }
 
 template <int TW, int TH>
@@ -753,6 +1084,15 @@ cudaError_t fwd_t(const Layout& L, const CfgDev& cfg, char* ws, float* image, cu
   a.n_tiles = L.NT;
   a.cap = L.cap;
   a.queue = ((Header*)(ws + L.header))->ctr;
+  const bool split = (cfg.flags & kFlagSplit) && !count && L.seg_slots > 0;
+  a.split_list = split ? (const uint4*)(ws + L.split_list) : nullptr;
+  a.tile_split = split ? (const uint32_t*)(ws + L.tile_slot) : nullptr;
+  a.slot_owner = split ? (const uint32_t*)(ws + L.slot_owner) : nullptr;
+  a.ext_owner = split ? (const uint32_t*)(ws + L.ext_owner) : nullptr;
+  a.split_term = split ? (uint32_t*)(ws + L.split_term) : nullptr;
+  a.seg_buf = split ? (float4*)(ws + L.seg_buf) : nullptr;
+  a.max_extra = split ? L.seg_max_extra : 0;
+  if (split) return fwd_split<TW, TH>(a, L, ws, st);
   const bool persistent = (cfg.flags & 8) != 0;
   return count ? fwd_launch<TW, TH, true>(a, L, persistent, st) : fwd_launch<TW, TH, false>(a, L, persistent, st);
 }
@@ -777,13 +1117,25 @@ cudaError_t bwd_t(const Layout& L, const CfgDev& cfg, char* ws, const float* dL,
   a.cap = L.cap;
   a.queue = ((Header*)(ws + L.header))->ctr + 2;
   const uint32_t n_blocks = L.NT * (TW * TH / 64);
+  // the same choice as the forward's: split lists unless counting pairs
+  const bool split = (cfg.flags & kFlagSplit) && !(cfg.flags & 2) && L.seg_slots > 0;
+  a.split_list = split ? (const uint4*)(ws + L.split_list) : nullptr;
+  a.tile_split = split ? (const uint32_t*)(ws + L.tile_slot) : nullptr;
+  a.ext_owner = split ? (const uint32_t*)(ws + L.ext_owner) : nullptr;
+  a.seg_buf = split ? (const float4*)(ws + L.seg_buf) : nullptr;
+  a.max_extra = split ? L.seg_max_extra : 0;
+  if (split) {
+    launch_dependent(render_bwd_kernel<TW, TH, true>, dim3((L.seg_max_extra + L.NT) * (TW * TH / 64)), dim3(32), 0,
+                     st, a);
+    return cudaGetLastError();
+  }
   if (cfg.flags & 8) {
     const uint32_t n = resident_ctas(render_bwd_persistent_kernel<TW, TH>, 32);
     if (n > 0)
-      return launch_dependent(render_bwd_persistent_kernel<TW, TH>, dim3(n < n_blocks ? n : n_blocks), dim3(32), 0,
-                              st, a);
+      return launch_dependent(render_bwd_persistent_kernel<TW, TH>, dim3(n < L.NT ? n : L.NT), dim3(32), 0, st,
+                              a);
   }
-  launch_dependent(render_bwd_kernel<TW, TH>, dim3(n_blocks), dim3(32), 0, st, a);
+  launch_dependent(render_bwd_kernel<TW, TH, false>, dim3(n_blocks), dim3(32), 0, st, a);
   return cudaGetLastError();
 }
 

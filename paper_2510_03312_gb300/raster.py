@@ -49,7 +49,8 @@ def config_struct(cfg: RasterConfig) -> U.ubs_config:
     c.alpha_min, c.alpha_max, c.T_min = cfg.alpha_min, cfg.alpha_max, cfg.T_min
     c.eps2d, c.near_plane, c.jac_clip = cfg.eps2d, cfg.near, cfg.jac_clip
     c.bg[:] = [float(x) for x in cfg.bg]
-    c.flags = (U.UBS_FLAG_TIGHT_CUT if cfg.tight_cut else 0) | (U.UBS_FLAG_PERSISTENT if cfg.persistent else 0)
+    c.flags = ((U.UBS_FLAG_TIGHT_CUT if cfg.tight_cut else 0) | (U.UBS_FLAG_PERSISTENT if cfg.persistent else 0) |
+               (U.UBS_FLAG_SPLIT_LISTS if cfg.split_lists else 0))
     return c
 
 

@@ -131,7 +131,8 @@ class RasterConfig:
     bg: tuple = (0.0, 0.0, 0.0)
     tight_cut: bool = True
     jac_clip: float = 1.3
-    persistent: bool = False  # launch form of the blend kernels (a schedule, not arithmetic)
+    persistent: bool = False   # launch form of the blend kernels (a schedule, not arithmetic)
+    split_lists: bool = False  # blend long tile lists in segments (same result up to rounding)
 
 
 # ----------------------------------------------------------------------------
@@ -330,6 +331,29 @@ def workload_uneven_mix(seed: int = 4, n_scenes: int = 8, n_jobs: int = 64,
         R, t = look_at(8.0 * u)
         views.append(make_view(R, t, W, H, time=tm, scene_id=s))
     return Workload(f"uneven_mix_{n_jobs}jobs_{n_scenes}scenes", scenes, views)
+
+
+def workload_deep_tile(seed: int = 5, P_sparse: int = 300_000, P_cluster: int = 60_000, width: int = 1600,
+                       height: int = 1060):
+    """A deep tile in front of a sparse view: N=3, P_sparse primitives
+    uniform in [-5,5]^3 and a cluster of P_cluster small, faint primitives
+    (scales log-U[0.002, 0.005], opacity sigmoid(N(-3, 0.3))) packed within
+    0.01 of a point at depth 4 on the optical axis, seen by one 1600x1060
+    camera on a radius-8 sphere: one tile's list holds most of the cluster
+    and its pixels do not saturate, so the whole list is walked."""
+    rng = np.random.default_rng(seed)
+    sp = make_scene(seed, 3, P_sparse, means="uniform", extent=5.0, rng=rng)
+    views = sphere_views(rng, 1, 8.0, width, height)
+    cl = make_scene(seed + 1, 3, P_cluster, means="uniform", extent=1.0, scale_range=(0.002, 0.005), rng=rng)
+    v = views[0]
+    centre = -np.asarray(v.R, np.float64).T @ np.asarray(v.t, np.float64)  # camera centre
+    ahead = np.asarray(v.R, np.float64)[2]                                  # optical axis
+    point = centre + 4.0 * ahead
+    cl.plane("mean_x")[:] = (point[:, None] + 0.01 * rng.uniform(-1.0, 1.0, (3, P_cluster))).astype(np.float32)
+    cl.plane("opacity")[:] = (1.0 / (1.0 + np.exp(3.0 - 0.3 * rng.standard_normal(P_cluster)))).astype(np.float32)
+    params = np.ascontiguousarray(np.concatenate([sp.params, cl.params], axis=1))
+    return Workload(f"deep_tile_n3_{P_sparse // 1000}k_{P_cluster // 1000}k_{width}x{height}",
+                    [Scene(3, ROT_QUAT, params)], views)
 
 
 def l1_target(seed: int, views) -> list:

@@ -31,6 +31,7 @@ UBS_FLAG_TIGHT_CUT = 1
 UBS_FLAG_COUNT_PAIRS = 2
 UBS_FLAG_ACCUMULATE_GRADS = 4
 UBS_FLAG_PERSISTENT = 8
+UBS_FLAG_SPLIT_LISTS = 16
 UBS_ACT_IDENTITY = 0
 UBS_ACT_SIGMOID = 1
 UBS_ACT_EXP = 2

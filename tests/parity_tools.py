@@ -144,9 +144,13 @@ def orc_pix(orc, vi):
     return slice(off, off + v.width * v.height)
 
 
-def check_grads(gpu, orc, ref_render, seed=7, tiles=None, tol=GRAD_TOL, views=None):
+def check_grads(gpu, orc, ref_render, seed=7, tiles=None, tol=GRAD_TOL, views=None, elem_tol=None):
     """GPU backward against the oracle's autograd gradient for the same
-    dL/dimage (zero on flagged pixels and outside the rendered tiles)."""
+    dL/dimage (zero on flagged pixels and outside the rendered tiles): per
+    parameter group within ``tol`` of the group's largest gradient, and
+    element by element within ``elem_tol`` (default ``tol``) relative plus
+    GRAD_FLOOR of the group's largest."""
+    elem_tol = tol if elem_tol is None else elem_tol
     rng = np.random.default_rng(seed)
     gl = []
     for vi, v in enumerate(orc.views):
@@ -175,8 +179,8 @@ def check_grads(gpu, orc, ref_render, seed=7, tiles=None, tol=GRAD_TOL, views=No
             assert e <= tol, f"scene {si} {name}: relative error {e:.2e}"
             # element by element, so that a wrong gradient of a faint
             # primitive is not hidden by a bright one of the same group
-            over = np.abs(a - ref) > tol * np.abs(ref) + GRAD_FLOOR * scale
+            over = np.abs(a - ref) > elem_tol * np.abs(ref) + GRAD_FLOOR * scale
             assert not over.any(), (f"scene {si} {name}: {int(over.sum())} elements beyond "
-                                    f"{tol:g} |g| + {GRAD_FLOOR:g} max|g|, e.g. "
+                                    f"{elem_tol:g} |g| + {GRAD_FLOOR:g} max|g|, e.g. "
                                     f"{[(float(a.flat[i]), float(ref.flat[i])) for i in np.flatnonzero(over)[:3]]}")
     return worst

@@ -50,37 +50,39 @@ def test_tune_picks_the_fastest_and_records_every_candidate():
     scenes, views, cfg = _batch()
     calls = []
 
-    def fake(tile, groups, persistent):
-        calls.append((tile, len(groups), persistent))
+    def fake(tile, groups, form):
+        calls.append((tile, len(groups), form))
         # fastest: 16x32 tiles in one persistent launch
-        return 1.0 + 0.1 * len(groups) + (0.0 if tile == (16, 32) else 0.5) + (0.0 if persistent else 0.05)
+        return 1.0 + 0.1 * len(groups) + (0.0 if tile == (16, 32) else 0.5) + (0.0 if form == "persistent" else 0.05)
 
     plan = A.tune(scenes, views, cfg, fake)
-    assert plan.tile == (16, 32) and plan.schedule == "one_launch" and plan.persistent
+    assert plan.tile == (16, 32) and plan.schedule == "one_launch" and plan.form == "persistent"
     assert len(plan.table) == len(A.TILES) * len(A.SCHEDULES) * len(A.FORMS) == len(calls)
     assert plan.ms == min(plan.table.values())
-    assert "16x32/one_launch/persistent" in plan.table and "16x32/one_launch" in plan.table
+    assert {"16x32/one_launch/persistent", "16x32/one_launch/grid", "16x32/one_launch/split"} <= set(plan.table)
+    c = plan.config(cfg)
+    assert (c.tile_w, c.tile_h, c.persistent, c.split_lists) == (16, 32, True, False)
 
 
 def test_tune_ties_go_to_the_first_candidate():
     scenes, views, cfg = _batch()
-    plan = A.tune(scenes, views, cfg, lambda tile, groups, persistent: 2.0)
+    plan = A.tune(scenes, views, cfg, lambda tile, groups, form: 2.0)
     assert plan.tile == A.TILES[0] and plan.schedule == next(iter(A.SCHEDULES))
-    assert plan.persistent == A.FORMS[0]
+    assert plan.form == A.FORMS[0]
 
 
 def test_plan_cache_hits_skip_measurement_and_persist(tmp_path):
     scenes, views, cfg = _batch()
     path = str(tmp_path / "plans.json")
     cache = A.PlanCache(path)
-    p1 = A.tune(scenes, views, cfg, lambda t, g, p: float(t[0] * t[1]) + len(g) - 0.5 * p, cache=cache)
+    p1 = A.tune(scenes, views, cfg, lambda t, g, f: float(t[0] * t[1]) + len(g) - 0.5 * (f == "split"), cache=cache)
 
-    def boom(tile, groups, persistent):
+    def boom(tile, groups, form):
         raise AssertionError("measured despite a cached plan")
 
     p2 = A.tune(scenes, views, cfg, boom, cache=A.PlanCache(path))
-    assert (p2.tile, p2.schedule, p2.groups, p2.persistent) == (p1.tile, p1.schedule, p1.groups, p1.persistent)
-    assert p2.persistent
+    assert (p2.tile, p2.schedule, p2.groups, p2.form) == (p1.tile, p1.schedule, p1.groups, p1.form)
+    assert p2.form == "split"
 
 
 def test_signature_follows_shapes_only():

@@ -109,18 +109,20 @@ def test_device_autotune_returns_a_valid_plan():
     assert len(plan.table) == 4 * len(A.FORMS)
 
 
+@pytest.mark.parametrize("form", ["persistent", "split"])
 @pytest.mark.parametrize("tile", A.TILES)
 @pytest.mark.parametrize("graph", [False, True])
-def test_persistent_blend_matches_the_grid(tile, graph):
-    """The persistent launch form of both blend kernels gives the grid
-    form's images bit for bit and the same gradients (up to float summation
-    order), on three steps in a row (its tile counters reset themselves),
-    eagerly and replayed from a captured graph."""
+def test_launch_forms_match_the_grid(form, tile, graph):
+    """The persistent launch form of both blend kernels, and the split-list
+    form on lists that need no split, give the grid form's images bit for
+    bit and the same gradients (up to float summation order), on three
+    steps in a row (the persistent tile counters and the split plan's
+    counters reset themselves), eagerly and replayed from a captured graph."""
     wl, ds = _jobs()
     cfg = replace(wl.cfg, tile_w=tile[0], tile_h=tile[1])
     per_view = _dl_per_view(wl.views)
     ref_img, ref_g = _reference(ds, wl.views, cfg, per_view)
-    b = raster.Batch(ds, wl.views, replace(cfg, persistent=True), A.one_launch(wl.scenes, wl.views))
+    b = raster.Batch(ds, wl.views, replace(cfg, **A.form_fields(form)), A.one_launch(wl.scenes, wl.views))
     b.size()
     dls = _batch_dls(b, per_view)
     graph_obj = b.capture(dls) if graph else None
