@@ -207,44 +207,29 @@ __device__ __forceinline__ bool ellipse_hits(const float4& p, float c, float rcu
   return inside || m <= rcut;
 }
 
-// Each warp lists, in order, the staged entries j < n whose support meets
-// its block (all of them when `all`), from the packed staging of the
-// two-pixel kernels; returns the count.
-__device__ __forceinline__ int warp_cull_list2(const float4* s_bb, const Staged2* s_st, const float* s_rc, int n,
-                                               bool all, float x0, float x1, float y0, float y1, uint8_t* list) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  int cnt = 0;
-  for (int k = 0; k < n; k += 32) {
-    const int j = k + lane;
-    bool hit = j < n && (all || box_hits(s_bb[j], x0, x1, y0, y1));
-    if (hit && !all) {
-      const float4 A = s_st[j].A, Bc = s_st[j].Bc;
-      hit = ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), s_st[j].Cc.x, s_rc[j], x0, x1, y0, y1);
-    }
-    const unsigned m = __ballot_sync(kFull, hit);
-    if (hit) list[cnt + __popc(m & lt)] = (uint8_t)j;
-    cnt += __popc(m);
-  }
-  __syncwarp();
-  return cnt;
+// Whether staged entry j's support (the ellipse r <= r_cut, widened) meets the
+// block [x0, x1] x [y0, y1]: its box first, then the ellipse itself.
+__device__ __forceinline__ bool entry_hits(const float4* s_bb, const Staged2* s_st, const float* s_rc, int j,
+                                           float x0, float x1, float y0, float y1) {
+  if (!box_hits(s_bb[j], x0, x1, y0, y1)) return false;
+  const float4 A = s_st[j].A, Bc = s_st[j].Bc;
+  return ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), s_st[j].Cc.x, s_rc[j], x0, x1, y0, y1);
 }
 
 // Forward blend: a CTA per tile, a warp per 8x8 block, two pixels per lane
 // (rows y and y + 4) carried in packed pairs, so that the pair evaluation
 // and the compositing update run once per entry for both pixels.  Each half
 // takes the operations of the scalar rule above in the same order.  The
-// warp walks its list two entries per step between checks that its 64
-// pixels are all done; the CTA stops loading batches once its tile's are.
+// warp walks the entries its cull keeps two per step between checks that
+// its 64 pixels are all done; the CTA stops loading batches once its
+// tile's are.
 template <int TW, int TH>
 struct FwdSmem {
   static constexpr int NT = TW * TH / 2;           // threads: two pixels each
   static constexpr int BS = NT < 256 ? NT : 256;  // records staged per batch
-  static constexpr int NW = NT / 32;
   Staged2 st[BS];
   float4 bb[BS];
   float rc[BS];
-  uint8_t list[NW][BS];
   int v;
   uint32_t next;
 };
@@ -314,7 +299,6 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
   const float wx0 = (float)bx + 0.5f, wx1 = wx0 + 7.0f, wy0 = (float)by + 0.5f, wy1 = wy0 + 7.0f;
   const float lg2_amin = lg2_approx(cfg.amin);
   const float2 one = make_float2(1.0f, 1.0f), neg1 = make_float2(-1.0f, -1.0f);
-  uint8_t* list = sm.list[threadIdx.x >> 5];
   float2 T = one, C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0;
   uint32_t last0 = 0, last1 = 0, np0 = 0, np1 = 0, nv = 0;
   bool done0 = !in0, done1 = !in1;
@@ -352,9 +336,6 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
     }
     __syncthreads();
     const int n = (int)min((uint32_t)BS, end - base);
-    // the counting variant walks every entry, to count every pair with r < 1,
-    // and also counts the entries the cull would have kept (visited)
-    const int cnt = warp_cull_list2(sm.bb, sm.st, sm.rc, n, COUNT, wx0, wx1, wy0, wy1, list);
     const uint32_t rel = base - list0;
     // one entry for both pixels; branch-free: a pair that is skipped (or
     // stops its pixel) adds c * 0 and keeps T, which leaves C and T exactly
@@ -368,9 +349,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
       if constexpr (COUNT) {
         np0 += (!done0 && r.x < 1.0f);
         np1 += (!done1 && r.y < 1.0f);
-        const float4 A = sj.A, Bc = sj.Bc;
-        nv += box_hits(sm.bb[j], wx0, wx1, wy0, wy1) &&
-              ellipse_hits(make_float4(-A.x, -A.z, Bc.x, Bc.z), sj.Cc.x, sm.rc[j], wx0, wx1, wy0, wy1);
+        nv += entry_hits(sm.bb, sm.st, sm.rc, j, wx0, wx1, wy0, wy1);
       }
       const bool u0 = !done0 && r.x < 1.0f && al0 >= cfg.amin;
       const bool u1 = !done1 && r.y < 1.0f && al1 >= cfg.amin;
@@ -392,10 +371,28 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
       last0 = ok0 ? rel + j + 1 : last0;
       last1 = ok1 ? rel + j + 1 : last1;
     };
-    for (int i = 0; i < cnt; i += 2) {
-      if (__all_sync(kFull, done0 && done1)) break;
-      blend(list[i]);
-      if (i + 1 < cnt) blend(list[i + 1]);
+    // 32 entries at a time: the warp's ballot of those whose support meets
+    // its block (every entry in the counting variant, which counts every pair
+    // with r < 1 and, apart, the entries the cull keeps), then those entries
+    // in order, two between checks that the block's pixels are all done;
+    // the entry index stays warp-uniform, from the ballot
+    bool all_done = false;
+    for (int k = 0; k < n && !all_done; k += 32) {
+      const int jl = k + (int)(threadIdx.x & 31);
+      const bool hit = jl < n && (COUNT || entry_hits(sm.bb, sm.st, sm.rc, jl, wx0, wx1, wy0, wy1));
+      unsigned mm = __ballot_sync(kFull, hit);
+      while (mm) {
+        if (__all_sync(kFull, done0 && done1)) {
+          all_done = true;
+          break;
+        }
+        blend(k + __ffs(mm) - 1);
+        mm &= mm - 1;
+        if (mm) {
+          blend(k + __ffs(mm) - 1);
+          mm &= mm - 1;
+        }
+      }
     }
   }
   if constexpr (SPLIT) {
@@ -741,7 +738,6 @@ struct BwdSmem {
   Staged2 st[WB];
   uint32_t rec[WB];
   float acc[10][WB + 1];  // +1: the 10 writer lanes hit 10 different banks
-  uint8_t list[WB];
 };
 
 struct BwdArgs {
@@ -853,14 +849,15 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& A, uint32_t g, int wb, 
       listed = box_hits(box, wx0, wx1, wy0, wy1) && ellipse_hits(st.p, st.q.x, rc, wx0, wx1, wy0, wy1);
     }
     const unsigned lm = __ballot_sync(kFull, listed);
-    if (listed) sm.list[__popc(lm & ((1u << lane) - 1u))] = (uint8_t)lane;
     __syncwarp();
     unsigned touched = 0;  // entries the block used (warp-uniform)
     // entry j of the batch is list position lo + j: the forward composited it
     // at a pixel only if lo + j < that pixel's last contributor
     const int lim0 = (int)last0 - lo, lim1 = (int)last1 - lo;
-    for (int i = __popc(lm) - 1; i >= 0; --i) {
-      const int j = sm.list[i];
+    // the listed entries back to front, the index warp-uniform from the ballot
+    for (unsigned rem = lm; rem != 0;) {
+      const int j = 31 - __clz(rem);
+      rem ^= 1u << j;
       const Staged2& sj = sm.st[j];
       const float4 D = sj.D, E = sj.E;
       PairEval2 e;

@@ -78,12 +78,24 @@ def _run_path(dev, scenes, views, cfg, guards):
     return r, image, dL
 
 
-@pytest.mark.parametrize("case", ["static_small", "n6_3views_tile8", "mixed_scenes"])
+@pytest.mark.parametrize("case", ["static_small", "n6_3views_tile8", "mixed_scenes", "persistent", "split_lists",
+                                  "split_lists_tile32"])
 def test_rasterizer_writes_stay_in_bounds(dev, case):
     rng = np.random.default_rng(3)
     if case == "static_small":
         wl = S.workload_static_small(P=3000, size=100)
         scenes, views, cfg = wl.scenes, wl.views, wl.cfg
+    elif case == "persistent":
+        scenes = [S.make_scene(7, 6, 6000, means="clusters", extent=2.0, n_clusters=8, rng=rng)]
+        views = S.sphere_views(rng, 3, 5.0, 121, 77, hemisphere=True)
+        cfg = S.RasterConfig(persistent=True)
+    elif case.startswith("split_lists"):
+        # two deep tiles (about 14,000 entries: seven segments each) beside short ones
+        scenes = [S.make_scene(65, 3, 24000, means="uniform", extent=0.04, scale_range=(0.01, 0.04))]
+        R, t = S.look_at((0.0, 0.0, -3.0))
+        views = [S.make_view(R, t, 96, 80)]
+        tile = (32, 32) if case.endswith("tile32") else (16, 16)
+        cfg = S.RasterConfig(split_lists=True, tile_w=tile[0], tile_h=tile[1])
     elif case == "n6_3views_tile8":
         scenes = [S.make_scene(4, 6, 6000, means="clusters", extent=2.0, n_clusters=8, rng=rng)]
         views = S.sphere_views(rng, 3, 5.0, 121, 77, hemisphere=True)
