@@ -514,7 +514,7 @@ def bench_train(r, ds, wl, args, dev, pk, n_sm, flush):
         "roofline": {
             "image_loss": {"bound": "alu", "fp32_ops": loss_ops, "bytes": loss_bytes,
                            "achieved": round(loss_ops / t_loss / 1e12, 3), "peak": round(alu_peak, 2),
-                           "unit": "TFLOP/s", "frac": round(loss_ops / t_loss / 1e12 / alu_peak, 4),
+                           "unit": "T lane-op/s", "frac": round(loss_ops / t_loss / 1e12 / alu_peak, 4),
                            "hbm_frac": round(loss_bytes / t_loss / 1e9 / pk["hbm_gbs"], 4)},
             "adam": {"bound": "hbm", "bytes": adam_bytes, "achieved": round(adam_bytes / t_adam / 1e9, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(adam_bytes / t_adam / 1e9 / pk["hbm_gbs"], 4)},
