@@ -127,18 +127,33 @@ constexpr int kCmpT = 256, kCmpI = kCmpTile / kCmpT;
 // depth pass blocks that kCmpTile consecutive output positions can fall in
 constexpr int kCmpSpan = (kCmpTile + kDsTile - 1) / kDsTile + 1;
 
+// The sum of v[0 .. n) over a block of NT threads (every thread calls it).
+template <int NT>
+__device__ __forceinline__ uint32_t block_sum_prefix(const uint32_t* __restrict__ v, uint32_t n, uint32_t* s_w) {
+  uint32_t part = 0;
+  for (uint32_t i = threadIdx.x; i < n; i += NT) part += v[i];
+  uint32_t total;
+  block_excl_scan<NT>(part, total, s_w);
+  return total;
+}
+
 // Keeps the records with tiles_touched > 0, in record order, as (depth key,
-// record) pairs starting at vis_prefix[block], and counts the first depth
-// pass's digits per (pass block, digit) into hist0.
+// record) pairs starting at the block's exclusive prefix of the visible
+// counts, and counts the first depth pass's digits per (pass block, digit)
+// into hist0.  The prefix is vis_prefix[block] (scanned by a kernel before),
+// or, where there are few compaction blocks (vis_count non-null), the sum of
+// the earlier blocks' counts, taken here: one launch fewer.
+constexpr uint32_t kFusePrefixMax = 2048;  // blocks up to which a block sums the earlier blocks' counts itself
 __global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restrict__ tiles,
                                                         const uint32_t* __restrict__ key, uint32_t R,
                                                         const uint32_t* __restrict__ vis_prefix,
+                                                        const uint32_t* __restrict__ vis_count,
                                                         uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
                                                         uint32_t* __restrict__ hist0, Header* hdr) {
   wait_prior_grid();
   __shared__ uint32_t s_w[kCmpT / 32 + 1];
   const uint32_t t = blockIdx.x;
-  const uint32_t excl = vis_prefix[t];
+  const uint32_t excl = vis_count ? block_sum_prefix<kCmpT>(vis_count, t, s_w) : vis_prefix[t];
   const uint32_t base = t * kCmpTile + threadIdx.x * kCmpI;
   bool f[kCmpI];
   uint32_t k[kCmpI];
@@ -301,18 +316,30 @@ __global__ void __launch_bounds__(kOsT, 5) downsweep_kernel(const uint32_t* __re
 
 constexpr int kEmT = 256, kEmI = kEmTile / kEmT;
 
-// First instance of each depth-sorted record: ioff[i] = icount_prefix[block]
-// + the exclusive scan of tiles_touched within the block.  The last block
-// records the instance total and flags an instance capacity overflow.
+// First instance of each depth-sorted record: ioff[i] = the block's
+// exclusive prefix of the instance counts + the exclusive scan of
+// tiles_touched within the block.  The prefix is icount[block], scanned in
+// place by a kernel before, or, with `summed` (few blocks), the sum of the
+// earlier blocks' raw counts, taken here.  The last block records the
+// instance total and flags an instance capacity overflow.
 __global__ void __launch_bounds__(kEmT) emit_offsets_kernel(const uint32_t* __restrict__ srec,
                                                             const uint32_t* __restrict__ tiles,
-                                                            const uint32_t* __restrict__ icount_prefix,
+                                                            const uint32_t* __restrict__ icount, bool summed,
                                                             uint32_t* __restrict__ ioff, uint32_t cap, Header* hdr) {
   wait_prior_grid();
   __shared__ uint32_t s_w[kEmT / 32 + 1];
+  __shared__ uint32_t s_pre;
   const uint32_t n = (uint32_t)hdr->n_visible;
   const uint32_t n_blocks = (n + kEmTile - 1) / kEmTile;
   for (uint32_t t = blockIdx.x; t < n_blocks; t += gridDim.x) {
+    if (summed) {
+      const uint32_t pre = block_sum_prefix<kEmT>(icount, t, s_w);
+      if (threadIdx.x == 0) s_pre = pre;
+    } else if (threadIdx.x == 0) {
+      s_pre = icount[t];
+    }
+    __syncthreads();
+    const uint32_t prefix = s_pre;
     const uint32_t base = t * kEmTile + threadIdx.x * kEmI;
     uint32_t c[kEmI], sum = 0;
 #pragma unroll
@@ -321,14 +348,14 @@ __global__ void __launch_bounds__(kEmT) emit_offsets_kernel(const uint32_t* __re
       sum += c[i];
     }
     uint32_t total;
-    uint32_t ex = icount_prefix[t] + block_excl_scan<kEmT>(sum, total, s_w);
+    uint32_t ex = prefix + block_excl_scan<kEmT>(sum, total, s_w);
 #pragma unroll
     for (int i = 0; i < kEmI; ++i) {
       if (base + i < n) ioff[base + i] = ex;
       ex += c[i];
     }
     if (t == n_blocks - 1 && threadIdx.x == 0) {
-      const uint64_t n_inst = (uint64_t)icount_prefix[t] + total;
+      const uint64_t n_inst = (uint64_t)prefix + total;
       hdr->n_inst = n_inst;
       if (n_inst > cap) set_status(hdr, kDevCapacity);
     }
@@ -711,11 +738,13 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* cvA = (uint32_t*)(ws + L.cvA);
   uint32_t* ckB = (uint32_t*)(ws + L.ckB);
   uint32_t* cvB = (uint32_t*)(ws + L.cvB);
-  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, vis, vis_prefix, L.n_cmp_tiles, 1, nullptr,
-                   nullptr, 0u, 1u);
+  const bool fuse_vis = L.n_cmp_tiles <= kFusePrefixMax;
+  if (!fuse_vis)
+    launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, vis, vis_prefix, L.n_cmp_tiles, 1, nullptr,
+                     nullptr, 0u, 1u);
   const size_t hd_stride = (size_t)L.n_dsort_tiles * 256;
-  launch_dependent(compact_kernel, dim3(L.n_cmp_tiles), dim3(kCmpT), 0, st, tiles, (const uint32_t*)(ws + L.key), L.R, vis_prefix, ckA, cvA,
-                                                  hd, hdr);
+  launch_dependent(compact_kernel, dim3(L.n_cmp_tiles), dim3(kCmpT), 0, st, tiles, (const uint32_t*)(ws + L.key), L.R,
+                   (const uint32_t*)vis_prefix, fuse_vis ? vis : nullptr, ckA, cvA, hd, hdr);
   // depth sort: 4 passes A->B->A->B->A; the last one counts instances per
   // emission block
   for (int p = 0; p < 4; ++p) {
@@ -734,10 +763,13 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* ikB = (uint32_t*)(ws + L.ikB);
   uint32_t* ivB = (uint32_t*)(ws + L.ivB);
   const ViewDev* views = (const ViewDev*)(ws + L.views);
-  launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, icount, icount, L.n_emit_tiles, 1, nullptr,
-                   (const uint64_t*)&hdr->n_visible, L.R, (uint32_t)kEmTile);
+  const bool fuse_icount = L.n_emit_tiles <= kFusePrefixMax;
+  if (!fuse_icount)
+    launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, icount, icount, L.n_emit_tiles, 1, nullptr,
+                     (const uint64_t*)&hdr->n_visible, L.R, (uint32_t)kEmTile);
   uint32_t* ioff = (uint32_t*)(ws + L.ioff);
-  launch_dependent(emit_offsets_kernel, dim3(min(L.n_emit_tiles, kEmitGrid)), dim3(kEmT), 0, st, cvA, tiles, icount, ioff, L.cap, hdr);
+  launch_dependent(emit_offsets_kernel, dim3(min(L.n_emit_tiles, kEmitGrid)), dim3(kEmT), 0, st, cvA, tiles,
+                   (const uint32_t*)icount, fuse_icount, ioff, L.cap, hdr);
   launch_dependent(emit_fill_kernel, dim3(min(L.n_isort_tiles, kEmitGrid)), dim3(kFlT), 0, st, cvA, ioff, (const uint2*)(ws + L.rect), views, L.V, L.cap,
                                                      ikA, ivA, L.tile_passes > 0 ? hi : nullptr, hdr);
   uint32_t* gh_tile = ghist + 4 * 256;
