@@ -130,9 +130,13 @@ __global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, 
   uint32_t* qk = s_qk[w];
   PrimIn<C> in;
   PrimVI<C> vi;
+  // the log-opacity bound below which a record is certainly culled (see
+  // view_condition): approximate log and quotient, inside the bound's margin
+  float cull_below = -INFINITY;
   if (live) {
     load_prim<C>(sc, p, in);
     prim_stage<C>(in, sc.rot_mode, vi);
+    if (cfg.amin > 0.0f) cull_below = __logf(__fdividef(cfg.amin, in.o)) - 0.01f;
     for (int i = 0; i < 3; ++i) prim[i][lane] = in.mx[i];
     for (int i = 0; i < 6; ++i) prim[3 + i][lane] = vi.Sc[i];
     prim[9][lane] = vi.beta_x;
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, 
     ViewCond c;
     uint32_t r = 0;
     if (live) {
-      view_condition<C>(in, vi, v, c);
+      view_condition<C>(in, vi, v, c, cull_below);
       r = v.rec_off + (uint32_t)p;
       cand = view_candidate(vi.valid, c, v, cfg);
       if (!cand) tiles[r] = 0;

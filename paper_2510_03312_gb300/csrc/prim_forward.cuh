@@ -270,8 +270,19 @@ struct ViewCond {
   float mc[3];
 };
 
+//
+// cull_below (a natural log): a record whose opacity is certain to fall
+// below alpha_min skips the opacity's exp/log and the mean shift, with
+// cond.oq = 0 (culled).  Since log(1 - tanh x) <= ln 2 - 2x and log32 of
+// 1 + u is never negative, each term of the exponent E is, in float32 (the
+// roundings are monotone), at most the matching term of
+// E_ub = sum 4 beta_q (ln 2 - 2 y^2); where E_ub < cull_below =
+// ln(alpha_min / o) - 0.01, o(q) = o exp(E) lies 1% below alpha_min, far
+// beyond the rounding of exp32 and of the product, and the full evaluation
+// would cull the record too.  No decision changes.
 template <int C>
-UBS_HD void view_condition(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& v, ViewCond& cond) {
+UBS_HD void view_condition(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewDev& v, ViewCond& cond,
+                           float cull_below = -INFINITY) {
   const float* Rv = v.R;
   float mc[3], shift[3] = {0.0f, 0.0f, 0.0f};
   float oq = in.o;
@@ -293,6 +304,19 @@ UBS_HD void view_condition(const PrimIn<C>& in, const PrimVI<C>& vi, const ViewD
       float acc = delta[k];
       for (int m = 0; m < k; ++m) acc = acc - vi.Lh[tri(k, m)] * y[m];
       y[k] = acc / vi.Lh[tri(k, k)];
+    }
+    float Eub = 0.0f;
+    for (int k = 0; k < C; ++k) {
+      const float bound = (4.0f * vi.beta_q[k]) * (spec::kLn2 - 2.0f * (y[k] * y[k]));
+      Eub = (k == 0) ? bound : Eub + bound;
+    }
+    if (Eub < cull_below) {  // culled whatever the exact exponent
+      cond.oq = 0.0f;
+      for (int i = 0; i < 3; ++i) {
+        cond.shift[i] = 0.0f;
+        cond.mc[i] = in.mx[i];
+      }
+      return;
     }
     float E = 0.0f;
     for (int k = 0; k < C; ++k) {
