@@ -92,7 +92,7 @@ enum {
   UBS_FLAG_PERSISTENT = 8, /* the blend kernels run as persistent grids (one CTA per resident
                               slot) that take tiles or 8x8 blocks from a counter in the same order,
                               instead of one CTA per tile or block; the results are the same */
-  UBS_FLAG_SPLIT_LISTS = 16 /* tile lists longer than 2048 entries are split into segments of 2048
+  UBS_FLAG_SPLIT_LISTS = 16, /* tile lists longer than 2048 entries are split into segments of 2048
                                blended by separate CTAs and merged front to back with the over
                                operator (C = C_1 + T_1 C_2, T = T_1 T_2), walking a segment again
                                for the pixels whose transmittance falls below T_min inside it; the
@@ -101,6 +101,14 @@ enum {
                                rounding.  Takes precedence over UBS_FLAG_PERSISTENT; ignored by
                                the UBS_FLAG_COUNT_PAIRS variant.  Needs a larger workspace (see
                                ubs_workspace_size) */
+  UBS_FLAG_NO_THRESHOLDS = 32, /* the gradient-check mode (central differences across a skip or
+                                  stop decision are meaningless): alpha_min = 0, alpha_max = 1
+                                  and T_min = 0 override the configuration's values, so every
+                                  pair with r < 1 is composited and no pixel stops early */
+  UBS_FLAG_CHECKED = 64 /* the blend kernels also record a record id of a tile list outside the
+                           problem's records (impossible in a consistent workspace) as the device
+                           status UBS_ERR_INTERNAL, which ubs_read_status reports; without it such
+                           an id is only clamped.  Results are otherwise the same */
 };
 
 /* One primitive set (Sec. 4.1-4.3).  Structure of arrays: every block below

@@ -169,6 +169,11 @@ CfgDev cfg_dev(const ubs_config& c) {
   d.bg[1] = c.bg[1];
   d.bg[2] = c.bg[2];
   d.flags = c.flags;
+  if (c.flags & kFlagNoThresholds) {  // the gradient-check mode: every pair with r < 1 is composited
+    d.amin = 0.0f;
+    d.amax = 1.0f;
+    d.tmin = 0.0f;
+  }
   return d;
 }
 

@@ -118,6 +118,8 @@ struct Layout {
 // UBS_FLAG_SPLIT_LISTS is set.
 constexpr uint32_t kSegLen = 2048;
 constexpr uint32_t kFlagSplit = 16;
+constexpr uint32_t kFlagNoThresholds = 32;
+constexpr uint32_t kFlagChecked = 64;
 
 // float record of one (view, primitive) for the blend kernels: 3 x float4
 //   [mu'_x hi, mu'_y hi, mu'_x lo, mu'_y lo]

@@ -71,6 +71,20 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 
+// A record id of a tile list, which is below R by construction: clamped, and
+// with UBS_FLAG_CHECKED an id out of range is also recorded in the device
+// status (UBS_ERR_INTERNAL), which ubs_read_status reports.
+__device__ __forceinline__ void set_status_dev(const Header* h, uint32_t s) {
+  atomicCAS(const_cast<uint32_t*>(&h->status), 0u, s);
+}
+__device__ __forceinline__ uint32_t record_id(uint32_t id, uint32_t R, const CfgDev& cfg, const Header* hdr) {
+  if (id >= R) {
+    if (cfg.flags & kFlagChecked) set_status_dev(hdr, kDevInternal);
+    return R - 1;
+  }
+  return id;
+}
+
 // A staged record, tile-relative: the screen mean is re-expressed relative to
 // the tile origin (hi - origin) + lo, exact for the subtraction and rounded
 // once, so that per pair dx = (pixel centre - origin) - mean costs one add.
@@ -330,7 +344,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs& A, uint32_t g, FwdSmem<T
     if (threadIdx.x < BS && idx < end) {
       Staged st;
       float4 box;
-      stage_record(A.rec4, min(A.ivals[idx], A.R - 1), ox, oy, lg2_amin, st, box, sm.rc[threadIdx.x]);  // ids < R
+      stage_record(A.rec4, record_id(A.ivals[idx], A.R, cfg, A.hdr), ox, oy, lg2_amin, st, box, sm.rc[threadIdx.x]);
       sm.st[threadIdx.x] = pack_staged(st);
       sm.bb[threadIdx.x] = box;
     }
@@ -477,9 +491,6 @@ __global__ void __launch_bounds__(TW * TH / 2, (TW * TH / 2 >= 128 ? 1024 / (TW 
   }
 }
 
-__device__ __forceinline__ void set_status_dev(const Header* h, uint32_t s) {
-  atomicCAS(const_cast<uint32_t*>(&h->status), 0u, s);
-}
 
 // The plan of split lists: every tile whose list holds more than kSegLen
 // entries gets a split index i, m = ceil(n / kSegLen) consecutive slots of
@@ -839,7 +850,7 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& A, uint32_t g, int wb, 
     const int n = hi - lo;
     bool listed = false;
     if (lane < n) {
-      const uint32_t r = min(A.ivals[start + lo + lane], A.R - 1);  // ids are < R by construction
+      const uint32_t r = record_id(A.ivals[start + lo + lane], A.R, cfg, A.hdr);
       Staged st;
       float4 box;
       float rc;

@@ -32,6 +32,8 @@ UBS_FLAG_COUNT_PAIRS = 2
 UBS_FLAG_ACCUMULATE_GRADS = 4
 UBS_FLAG_PERSISTENT = 8
 UBS_FLAG_SPLIT_LISTS = 16
+UBS_FLAG_NO_THRESHOLDS = 32
+UBS_FLAG_CHECKED = 64
 UBS_ACT_IDENTITY = 0
 UBS_ACT_SIGMOID = 1
 UBS_ACT_EXP = 2

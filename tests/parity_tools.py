@@ -56,8 +56,13 @@ def check_preprocess(gpu, orc, views=None):
         g = gpu["rec"][o:o + P][v]
         assert np.array_equal(g[:, 4:7].view(np.uint32), pre["conic"].T[v].view(np.uint32)), "conic bits"
         assert np.array_equal(g[:, 8].view(np.uint32), pre["beta_x"][v].view(np.uint32)), "beta bits"
-        oq = np.exp2(g[:, 7].astype(np.float64))
-        np.testing.assert_allclose(oq, pre["opacity"][v], rtol=2e-6)
+        # the record holds log2 o(q) in float32 (the float32 o(q) itself is
+        # the rule set's, bit-exact): within 2 ulps of its float32 value
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lo = np.log2(pre["opacity"][v].astype(np.float64))  # -inf where o(q) underflowed to 0
+            gl = g[:, 7].astype(np.float64)
+            ok_lo = (gl == lo) | (np.abs(gl - lo) <= 2.4e-7 * np.maximum(np.abs(lo), 1.0))
+        assert ok_lo.all(), f"view {vi}: log2 o(q) off at {np.flatnonzero(~ok_lo)[:5]}"
         if rec64 is None:
             continue
         mu = g[:, 0:2].astype(np.float64) + g[:, 2:4].astype(np.float64)
@@ -76,10 +81,14 @@ def check_bins(gpu, orc):
     assert np.array_equal(starts[:-1], b["ranges"][:, 0]) and np.array_equal(starts[1:], b["ranges"][:, 1])
 
 
-def check_images(gpu, orc, recs=None, tiles=None, tol=IMG_TOL):
+def check_images(gpu, orc, recs=None, tiles=None, tol=IMG_TOL, check_last=True):
     """Every pixel within tol of the float64 value, or of one admissible
     result where the oracle flagged a near-threshold decision.  Returns
-    (max error on unflagged pixels, flagged pixel count)."""
+    (max error on unflagged pixels, flagged pixel count).  ``check_last``:
+    also the last contributor of every unflagged pixel (not in the
+    gradient-check mode, where a pair whose r rounds across 1 with alpha
+    near 0 counts as composited on one side only and moves the index
+    without changing colour or T)."""
     ref = orc.render(tiles=tiles, recs=recs)
     worst, nflag = 0.0, 0
     for vi in range(len(orc.views)):
@@ -104,8 +113,9 @@ def check_images(gpu, orc, recs=None, tiles=None, tol=IMG_TOL):
             continue
         T = gpu["T"][orc_pix(orc, vi)].reshape(r.shape[1:])
         assert np.abs(T - ref["T"][vi].numpy())[ok].max() <= tol
-        last = gpu["last"][orc_pix(orc, vi)].reshape(r.shape[1:]).astype(np.int64)
-        assert np.array_equal(last[ok], ref["last"][vi].numpy()[ok])
+        if check_last:
+            last = gpu["last"][orc_pix(orc, vi)].reshape(r.shape[1:]).astype(np.int64)
+            assert np.array_equal(last[ok], ref["last"][vi].numpy()[ok])
     return worst, nflag, ref
 
 
