@@ -208,20 +208,13 @@ def kernels_per_step(r):
     V, S = len(r.views), len(r.scenes)
     NT = sum(((v.width + r.cfg.tile_w - 1) // r.cfg.tile_w) * ((v.height + r.cfg.tile_h - 1) // r.cfg.tile_h)
              for v in r.views)
-    bits = max(0, math.ceil(math.log2(NT))) if NT > 1 else 0
-    tile_passes = (bits + 7) // 8
     upload = (V + 15) // 16
     pre = upload + S
-    # compact (after a scan of the visible counts unless there are at most
-    # 2048 compaction blocks, which then sum the earlier blocks' counts
-    # themselves), 4 depth passes (scan + downsweep), emission offsets (after a
-    # scan unless at most 2048 emission blocks) and fill, tile-key passes
-    # (scan + downsweep), ranges, then the tile order over 1024 tiles where
-    # the capacity allows dense lists (one kernel up to 16384 tiles)
+    # the count, the scan (two kernels, three over more than 2048 x 1024
+    # tiles; the second also makes the tile order), the scatter, the
+    # per-tile sort and the merge of long lists
     R = sum(r.scenes[v.scene_id].P for v in r.views)
-    scans = (0 if (R + 2047) // 2048 <= 2048 else 1) + (0 if (R + 1023) // 1024 <= 2048 else 1)
-    order = 0 if (NT <= 1024 or r.capacity < 64 * NT) else (1 if NT <= 16384 else 2)
-    sort = scans + 1 + 4 * 2 + 2 + 2 * tile_passes + 1 + order
+    sort = 0 if R == 0 else (1 + 2 + (1 if (NT + 1023) // 1024 > 2048 else 0) + 3)
     # forward blend; zeroing of the visible records' gradient sums, backward
     # blend; parameter backward per scene
     return pre + sort + 1 + 2 + S

@@ -7,9 +7,6 @@
 #include "kernels.cuh"
 
 namespace ubs {
-void sort_tile_sizes(uint32_t R, uint32_t cap, uint32_t* n_cmp, uint32_t* n_emit, uint32_t* n_dsort,
-                     uint32_t* n_isort);
-
 namespace {
 
 constexpr int kUploadChunk = 16;
@@ -75,7 +72,7 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
     NT += tx * ty;
     NPIX += (uint64_t)w.width * w.height;
   }
-  if (R > 0x7fffffffull || NT > 0x7fffffffull || NPIX > 0x7fffffffull) return UBS_ERR_INVALID_ARG;
+  if (R > 0x7fffffffull || NT * kTileSub > 0x7fffffffull || NPIX > 0x7fffffffull) return UBS_ERR_INVALID_ARG;
   memset(&L, 0, sizeof(L));
   L.V = pr->n_views;
   L.S = pr->n_scenes;
@@ -83,11 +80,11 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.NT = (uint32_t)NT;
   L.NPIX = (uint32_t)NPIX;
   L.cap = (uint32_t)(pr->instance_capacity > 0 ? pr->instance_capacity : 1);
-  int bits = 0;
-  while ((1ull << bits) < NT) ++bits;
-  L.tile_bits = bits;
-  L.tile_passes = (bits + 7) / 8;
-  sort_tile_sizes(L.R, L.cap, &L.n_cmp_tiles, &L.n_emit_tiles, &L.n_dsort_tiles, &L.n_isort_tiles);
+  L.n_scan_blocks = (L.NT + kScanTiles - 1) / kScanTiles;
+  uint64_t words = 0;
+  for (int v = 0; v < pr->n_views; ++v) words += (uint64_t)(pr->scenes[pr->views[v].scene_id].P + 31) / 32;
+  L.mask_words = (uint32_t)words;
+  L.max_items = L.NT + L.cap / kSortChunk + 1;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -101,31 +98,24 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.tiles = take((size_t)L.R * 4);
   L.rect = take((size_t)L.R * 8);
   L.g2d = take((size_t)L.R * kGradFloats * 4);
-  L.ckA = take((size_t)L.R * 4);
-  L.cvA = take((size_t)L.R * 4);
-  L.ckB = take((size_t)L.R * 4);
-  L.cvB = take((size_t)L.R * 4);
-  L.ikA = take((size_t)L.cap * 4);
-  L.ivA = take((size_t)L.cap * 4);
-  L.ikB = take((size_t)L.cap * 4);
-  L.ivB = take((size_t)L.cap * 4);
+  L.tcount = take((size_t)L.NT * kTileSub * 4 + 4 * 132 * 4 + 32 * 32 * 4);
+  L.order_count = L.tcount + (size_t)L.NT * kTileSub * 4;
+  L.vis_part = L.order_count + 4 * 132 * 4;
+  L.cursor = take((size_t)L.NT * kTileSub * 4);
+  L.vis_mask = take((size_t)L.mask_words * 4);
+  L.bucket = take((size_t)L.cap * 4);
+  L.ivals = take((size_t)L.cap * 4);
+  L.chunk64 = take((size_t)L.cap * 8);
+  L.tmp64 = take((size_t)L.cap * 8);
+  L.items = take((size_t)L.max_items * 8);
+  L.scan_part = take(((size_t)2 * L.n_scan_blocks + 1) * 16);
   L.tstart = take((size_t)(L.NT + 1) * 4);
   L.tile_order = take((size_t)L.NT * 4);
-  L.vis_count = take((size_t)L.n_cmp_tiles * 4);
-  L.vis_prefix = take((size_t)L.n_cmp_tiles * 4);
-  L.ioff = take((size_t)L.R * 4);
-  // the primitives some view sees, per scene (kept outside the region that
-  // ubs_bin_sort zeroes below)
+  // the primitives some view sees, per scene
   uint64_t Ptot = 0;
   for (int sc = 0; sc < pr->n_scenes; ++sc) Ptot += (uint64_t)pr->scenes[sc].P;
   L.act_list = take((size_t)Ptot * 4);
   L.act_count = take((size_t)kMaxScenes * 4);
-  // per-pass counts, rewritten whole by every ubs_bin_sort
-  L.hist_d = take((size_t)4 * L.n_dsort_tiles * 256 * 4);
-  L.hist_i = take((size_t)L.tile_passes * L.n_isort_tiles * 256 * 4);
-  L.icount = take((size_t)L.n_emit_tiles * 4);
-  L.ghist = take(7 * 256 * 4);
-  L.order_count = take(2 * 132 * 4);  // zeroed with the per-pass counts
   L.Tfin = take((size_t)L.NPIX * 4);
   L.last = take((size_t)L.NPIX * 4);
   L.pairs = take((size_t)L.NPIX * 8);  // pairs with r < 1, then visited entries
@@ -246,11 +236,11 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
   if (e != cudaSuccess) return UBS_ERR_CUDA;
   e = cudaMemsetAsync(w + L.act_count, 0, (size_t)L.S * 4, stream);
   if (e != cudaSuccess) return UBS_ERR_CUDA;
-  e = cudaMemsetAsync(w + L.vis_count, 0, (size_t)L.n_cmp_tiles * 4, stream);
+  e = cudaMemsetAsync(w + L.tcount, 0, (size_t)L.NT * kTileSub * 4 + 4 * 132 * 4 + 32 * 32 * 4, stream);
   if (e != cudaSuccess) return UBS_ERR_CUDA;
-  // view table: per-view constants, tile/record/pixel offsets
+  // view table: per-view constants, tile/record/pixel/mask offsets
   ViewDev* views = (ViewDev*)(w + L.views);
-  uint32_t tile_off = 0, rec_off = 0, pix_off = 0;
+  uint32_t tile_off = 0, rec_off = 0, pix_off = 0, mask_off = 0;
   for (int c0 = 0; c0 < L.V; c0 += kUploadChunk) {
     ViewChunk chunk;
     memset(&chunk, 0, sizeof(chunk));
@@ -273,9 +263,11 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
       d.tile_off = tile_off;
       d.rec_off = rec_off;
       d.pix_off = pix_off;
+      d.mask_off = mask_off;
       tile_off += (uint32_t)(d.tiles_x * d.tiles_y);
       rec_off += (uint32_t)pr->scenes[v.scene_id].P;
       pix_off += (uint32_t)(v.width * v.height);
+      mask_off += (uint32_t)((pr->scenes[v.scene_id].P + 31) / 32);
     }
     upload_views_kernel<<<1, kUploadChunk, 0, stream>>>(chunk, n, views + c0);
     e = cudaGetLastError();
@@ -379,7 +371,12 @@ ubs_status ubs_read_status(const ubs_problem* pr, void* ws, size_t ws_bytes, ubs
     return UBS_ERR_CUDA;
   out->status = (int32_t)h.status;
   out->reserved = 0;
-  out->visible_records = (int64_t)h.n_visible;
+  uint32_t part[32 * 32];
+  if (cudaMemcpy(part, (char*)ws + L.vis_part, sizeof(part), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return UBS_ERR_CUDA;
+  int64_t vis = 0;
+  for (int i = 0; i < 32; ++i) vis += part[32 * i];
+  out->visible_records = vis;
   out->instances = (int64_t)h.n_inst;
   return UBS_OK;
 }

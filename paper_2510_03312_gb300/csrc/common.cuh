@@ -26,7 +26,8 @@ struct ViewDev {
   uint32_t tile_off;  // first global tile id of the view
   uint32_t rec_off;   // first record of the view
   uint32_t pix_off;   // first pixel of the view (images are packed)
-  uint32_t pad[3];
+  uint32_t mask_off;  // first word of the view's visibility mask (a bit per primitive)
+  uint32_t pad[2];
 };
 static_assert(sizeof(ViewDev) == 112, "ViewDev layout");
 
@@ -66,9 +67,10 @@ struct SceneGradDev {
 // Device status block at the start of the workspace.
 struct Header {
   uint32_t status;       // ubs_status of device-side work (0 = ok)
-  uint32_t pad0;
-  uint64_t n_visible;    // records with tiles_touched > 0
+  uint32_t n_items;      // work items of the per-tile sort (0 after a capacity overflow)
   uint64_t n_inst;       // instances required
+  uint32_t n_long;       // of those, the chunks of lists longer than kSortChunk (listed first)
+  uint32_t pad0;
   uint32_t ctr[32];      // dynamic tile counters, one per single-pass kernel
 };
 
@@ -79,25 +81,26 @@ struct Layout {
   uint32_t NT;      // tiles
   uint32_t NPIX;    // pixels
   uint32_t cap;     // instance capacity
-  int32_t tile_bits, tile_passes;
-  uint32_t n_cmp_tiles;   // compaction blocks
-  uint32_t n_emit_tiles;  // emission offset blocks (records)
-  uint32_t n_dsort_tiles; // depth radix pass blocks (records)
-  uint32_t n_isort_tiles; // tile-key radix pass blocks = emission fill blocks (instances)
+  uint32_t n_scan_blocks;  // blocks of the tile-count scan (kScanTiles tiles each)
+  uint32_t mask_words;     // words of the visibility masks: the sum over views of ceil(P / 32)
+  uint32_t max_items;      // bound on the per-tile sort's work items: NT + cap / kSortChunk + 1
   size_t header, views, rec4, key, tiles, rect, g2d;
-  size_t ckA, cvA, ckB, cvB;
-  size_t ikA, ivA, ikB, ivB;
+  size_t tcount;     // instances per (tile, sub-bucket) [kTileSub][NT], then per length bucket
+                     // the totals and cursors of the tile order and of the short lists' sort
+                     // items [4 x 132], then the visible records' partial sums [32 x 32]
+                     // (zeroed together by ubs_preprocess)
+  size_t cursor;     // next free slot of each (tile, sub-bucket) [kTileSub][NT]
+  size_t vis_mask;   // per view, a bit per primitive: visible (written whole by preprocess) [mask_words]
+  size_t bucket;     // the instances grouped by tile, unordered within a tile [cap]
+  size_t ivals;      // the sorted instance lists [cap]
+  size_t chunk64;    // sorted chunks (depth << 32 | record) of lists longer than kSortChunk [cap]
+  size_t tmp64;      // the other buffer of their merge rounds [cap]
+  size_t items;      // (tile, chunk) work items of the per-tile sort [max_items]
+  size_t scan_part;  // per scan block: instances (u64) and items, then their exclusive prefixes
   size_t tstart;
   size_t tile_order;   // the order the blend kernels take the tiles in [NT]
-  size_t order_count;  // tiles per list-length bucket and bucket cursors [2 x 132]
-  size_t vis_count;  // visible records per compaction block [n_cmp_tiles] (made by preprocess)
-  size_t vis_prefix; // its exclusive prefix [n_cmp_tiles]
-  size_t ioff;       // first instance of each depth-sorted record [R]
-  // rewritten whole by every bin_sort (no zeroing needed)
-  size_t hist_d;     // per (pass block, digit) counts of the 4 depth passes [4][n_dsort_tiles][256]
-  size_t hist_i;     // the same for the tile-key passes [tile_passes][n_isort_tiles][256]
-  size_t icount;     // instances per emission block [n_emit_tiles]
-  size_t ghist;      // digit totals per pass [4 + 3][256]
+  size_t order_count;  // the length buckets' totals and cursors [4 x 132] (after tcount)
+  size_t vis_part;     // visible records in 32 partial sums, 128 bytes apart [32 x 32] (after order_count)
   size_t act_list;   // per scene (at the sum of the earlier scenes' P): primitives visible in some view
   size_t act_count;  // their number per scene [kMaxScenes]
   size_t Tfin, last, pairs;
@@ -132,11 +135,15 @@ constexpr int kRecFloats = 12;
 constexpr int kGradFloats = 12;
 
 
-// block sizes of the binning kernels (items per block)
-constexpr int kCmpTile = 2048;  // compaction
-constexpr int kDsTile = 2048;   // one depth radix pass (records)
-constexpr int kIsTile = 2048;   // one tile-key radix pass and one emission fill block (instances)
-constexpr int kEmTile = 1024;   // instance offsets of the depth-sorted records
+// the binning: tiles per block of the tile-count scan; sub-buckets per tile
+// (a record's is its index mod kTileSub: the atomic adds on one tile's
+// counters spread over that many addresses); the longest list one warp
+// sorts whole (longer lists are sorted in chunks of this many entries and
+// then merged)
+constexpr uint32_t kScanTiles = 1024;
+constexpr uint32_t kTileSub = 8;
+constexpr uint32_t kSortChunk = 1024;
+constexpr int kCtrSortItems = 8;  // header counter of the per-tile sort's next item
 
 enum DevStatus : uint32_t { kDevOk = 0, kDevCapacity = 3, kDevTimeout = 5, kDevInternal = 6 };
 

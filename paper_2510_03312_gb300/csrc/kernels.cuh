@@ -44,6 +44,46 @@ inline bool order_possible(const Layout& L) {
   return L.NT > kOrdMinTiles && (uint64_t)L.cap >= (uint64_t)kOrdDense * L.NT;
 }
 
+// The binning walks a record's rectangle of up to kSoloTiles tiles in its
+// own lane and a larger one with the whole warp.
+constexpr uint32_t kSoloTiles = 8;
+
+// Calls f(g, rec) for every tile g of each active lane's rectangle that has
+// more than kSoloTiles tiles (n tiles: columns x0 <= tx < x1 of
+// rc.x/rc.y's low halves, rows y0 <= ty < y1 of their high halves, at tile
+// toff + ty tsx + tx of the view), the active lanes, which must be converged
+// at the call, taking the rectangles in turn.
+template <class F>
+__device__ __forceinline__ void walk_large_rects(uint32_t n, uint2 rc, uint32_t toff, uint32_t tsx, uint32_t rec,
+                                                 F&& f) {
+  const unsigned act = __activemask();
+  unsigned big = __ballot_sync(act, n > kSoloTiles);
+  if (!big) return;
+  const unsigned lane = threadIdx.x & 31;
+  const uint32_t nact = (uint32_t)__popc(act), me = (uint32_t)__popc(act & ((1u << lane) - 1u));
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const uint32_t sn = __shfl_sync(act, n, src), sx = __shfl_sync(act, rc.x, src), sy = __shfl_sync(act, rc.y, src);
+    const uint32_t so = __shfl_sync(act, toff, src), ss = __shfl_sync(act, tsx, src), sr = __shfl_sync(act, rec, src);
+    const uint32_t sx0 = sx & 0xFFFFu, w = (sy & 0xFFFFu) - sx0, sy0 = sx >> 16;
+    for (uint32_t k = me; k < sn; k += nact) f(so + (sy0 + k / w) * ss + sx0 + k % w, sr);
+  }
+}
+
+// The tiles of a rectangle of at most kSoloTiles tiles, row-major; entries
+// k >= n are left as they are.
+__device__ __forceinline__ void solo_tiles(uint32_t n, uint2 rc, uint32_t toff, uint32_t tsx,
+                                           uint32_t (&g)[kSoloTiles]) {
+  const uint32_t x0 = rc.x & 0xFFFFu, x1 = rc.y & 0xFFFFu;
+  uint32_t tx = x0, ty = rc.x >> 16;
+#pragma unroll
+  for (uint32_t k = 0; k < kSoloTiles; ++k) {
+    if (k < n) g[k] = toff + ty * tsx + tx;
+    if (++tx == x1) tx = x0, ++ty;
+  }
+}
+
 template <typename... Params, typename... Args>
 cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              Args... args) {

@@ -36,7 +36,7 @@ template <int C>
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList vl, const ViewDev* __restrict__ views,
                                                          CfgDev cfg, float4* __restrict__ rec4,
                                                          uint32_t* __restrict__ key, uint32_t* __restrict__ tiles,
-                                                         uint2* __restrict__ rect, uint32_t* __restrict__ vis_count,
+                                                         uint2* __restrict__ rect, uint32_t* __restrict__ vis_mask,
                                                          uint32_t* __restrict__ act_list, uint32_t* act_count) {
   wait_prior_grid();
   extern __shared__ ViewDev s_views[];
@@ -58,12 +58,11 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList v
     const uint32_t r = v.rec_off + (uint32_t)p;
     tiles[r] = o.tiles;
     {
-      // visible records per compaction block (one add per group of lanes)
+      // the warp's 32 primitives (p aligned to 32) are one word of the
+      // view's visibility mask: lane l's bit for primitive 32 (p / 32) + l
       const unsigned act = __activemask();
-      const uint32_t blk = r / kCmpTile;
-      const unsigned peers = __match_any_sync(act, blk);
-      const unsigned vis = __ballot_sync(act, o.valid) & peers;
-      if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1) && vis) atomicAdd(vis_count + blk, (uint32_t)__popc(vis));
+      const unsigned vis = __ballot_sync(act, o.valid);
+      if ((threadIdx.x & 31) == (unsigned)(__ffs(act) - 1)) vis_mask[v.mask_off + (uint32_t)(p >> 5)] = vis;
     }
     if (o.valid) {
       key[r] = __float_as_uint(o.depth);
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, 
                                                                 const ViewDev* __restrict__ views, CfgDev cfg,
                                                                 float4* __restrict__ rec4, uint32_t* __restrict__ key,
                                                                 uint32_t* __restrict__ tiles, uint2* __restrict__ rect,
-                                                                uint32_t* __restrict__ vis_count,
+                                                                uint32_t* __restrict__ vis_mask,
                                                                 uint32_t* __restrict__ act_list, uint32_t* act_count) {
   wait_prior_grid();
   extern __shared__ ViewDev s_views[];
@@ -117,8 +116,10 @@ __global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, 
   __shared__ float s_qf[kQWarps][4][kQCap];
   __shared__ uint32_t s_qr[kQWarps][kQCap], s_qk[kQWarps][kQCap];
   __shared__ uint32_t s_any[kQWarps];
+  __shared__ uint32_t s_vis[kQWarps][kMaxViews];  // per warp and view: the visibility mask word
   for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
   if (threadIdx.x < kQWarps) s_any[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < kQWarps * vl.n; i += blockDim.x) s_vis[i / vl.n][i % vl.n] = 0;
   __syncthreads();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = p < sc.P;  // every lane stays: the queue is warp-synchronous
@@ -160,15 +161,8 @@ __global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, 
     ViewOut o;
     view_project(mx, Sc, beta_x, true, c, s_views[k], cfg, o);
     tiles[r] = o.tiles;
-    {
-      // visible records per compaction block (one add per group of lanes)
-      const unsigned act = __activemask();
-      const uint32_t blk = r / kCmpTile;
-      const unsigned peers = __match_any_sync(act, blk);
-      const unsigned vis = __ballot_sync(act, o.valid) & peers;
-      if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1) && vis) atomicAdd(vis_count + blk, (uint32_t)__popc(vis));
-    }
     if (o.valid) {
+      atomicOr(&s_vis[w][k], 1u << owner);
       key[r] = __float_as_uint(o.depth);
       rect[r] = make_uint2((uint32_t)o.tx0 | ((uint32_t)o.ty0 << 16), (uint32_t)o.tx1 | ((uint32_t)o.ty1 << 16));
       rec4[3 * (size_t)r + 0] = make_float4(o.mu_hi[0], o.mu_hi[1], o.mu_lo[0], o.mu_lo[1]);
@@ -207,6 +201,11 @@ __global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, 
   }
   if (lane < qn) project(lane);
   __syncwarp();
+  // the warp's visibility mask word of each view (its primitives start at a
+  // multiple of 32)
+  const int64_t p0 = p - lane;
+  if (p0 < sc.P)
+    for (int k = lane; k < vl.n; k += 32) vis_mask[s_views[k].mask_off + (uint32_t)(p0 >> 5)] = s_vis[w][k];
   // scenes with several views: the primitives some view sees, listed for the
   // parameter backward (one add per warp)
   const bool any = live && ((s_any[w] >> lane) & 1u);
@@ -253,7 +252,7 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
   uint32_t* key = (uint32_t*)(ws + L.key);
   uint32_t* tiles = (uint32_t*)(ws + L.tiles);
   uint2* rect = (uint2*)(ws + L.rect);
-  uint32_t* vis = (uint32_t*)(ws + L.vis_count);
+  uint32_t* vis = (uint32_t*)(ws + L.vis_mask);
   switch (sc.N) {
     case 3: launch_dependent(preprocess_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
     case 4: launch_dependent(preprocess_queued_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;

@@ -1,29 +1,35 @@
 // sort.cu -- B1-B3: tile binning, front-to-back order and tile ranges.
 //
 // The instance order is (global tile, float32 depth, record index).  It is
-// produced as two stable LSD radix sorts instead of one sort of 64-bit
-// (tile, depth) keys over all instances:
-//   1. compact the visible records (order-preserving, so ties stay in record
-//      order) and sort them by depth (4 passes of 8 bits over records);
-//   2. emit the instances of the depth-sorted records in that order (every
-//      record's tiles row-major in its rectangle);
-//   3. sort the instances by tile id (ceil(log2 tiles / 8) passes);
-//   4. find each tile's range from the boundaries of the sorted tile keys.
-// Because both sorts are stable, each tile's list ends up in (depth, record)
-// order: the same order as a single sort by the 64-bit key, at roughly half
-// the bytes (depth passes touch records, not instances).
+// made as a most-significant-digit radix sort whose first digit is the whole
+// tile id, the rest of the key being sorted inside each tile:
+//   1. count: every visible record (a set bit of the visibility masks the
+//      preprocess writes, one bit per primitive and view) adds one to a
+//      counter of each tile of its rectangle, one of kTileSub sub-buckets
+//      by record index, so that the adds on a busy tile spread over several
+//      addresses;
+//   2. scan: the exclusive prefix of the counts gives each tile's range
+//      (B3) and the start of its bucket; the scan also lists the work items
+//      of step 4 (one per tile, or one per kSortChunk entries of a longer
+//      list) and, where lists are long, the order in which the blend kernels
+//      take the tiles;
+//   3. scatter: every visible record writes its index into the bucket of
+//      each of its tiles, at a slot taken from its sub-bucket's cursor (an
+//      atomic add); the order inside a bucket is the order the adds ran in;
+//   4. per-tile sort: one warp sorts a bucket by the 64-bit key
+//      (depth bits << 32 | record) in registers, with a bitonic network;
+//      a list longer than kSortChunk entries is sorted in chunks of that
+//      many entries, and
+//   5. merge: one CTA per such list merges its sorted chunks pairwise in
+//      rounds (merge path: each thread an equal share of the outputs), in
+//      shared memory up to kMergeSeg entries, then in global memory.
+// A record meets a tile once, so the keys of a tile are distinct and the
+// result does not depend on the bucket order: it is the order a stable
+// sort by (tile, depth) of the records in index order gives.
 //
-// No kernel waits on another block: every step that needs the offsets of
-// earlier blocks is split at a kernel boundary (count, then scan, then
-// place).  The counts a step needs are made by the kernel before it, while
-// it writes that step's input: the preprocess kernel counts visible records
-// per compaction block; the compaction counts the first depth pass's digits
-// per (pass block, digit); each radix pass counts the next pass's digits for
-// the positions it writes (the last depth pass counts instances per
-// emission block instead); the emission counts the first tile pass's
-// digits.  A column scan turns counts into each block's exclusive offsets
-// (and digit totals), and the pass then ranks its items locally (stable)
-// and places them.
+// No kernel waits on another block: every step's inputs are made by the
+// kernels before it.  A work item of the per-tile sort holds at most
+// kSortChunk entries, so the items need no ordering to balance the grid.
 #include "kernels.cuh"
 
 namespace ubs {
@@ -36,519 +42,79 @@ __device__ __forceinline__ void set_status(Header* h, uint32_t s) { atomicCAS(&h
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-// Lanes of the warp holding the same 9-bit value d (digits < 256, 0x100 for
-// "no item"): one ballot per bit, each lane keeping the lanes that agree.
-__device__ __forceinline__ uint32_t peer_mask(uint32_t d) {
-  uint32_t peers = kFull;
-#pragma unroll
-  for (int b = 0; b < 9; ++b) {
-    const bool bit = (d >> b) & 1u;
-    const uint32_t bal = __ballot_sync(kFull, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
-  const uint32_t lane = lane_id();
+// Exclusive scan of one value per thread over a block of NT threads
+// (NT / 32 <= 32); total receives the block's sum.  s_w must hold NT/32 + 1
+// values.  Must be called by every thread.
+template <typename T, int NT>
+__device__ __forceinline__ T block_excl_scan(T v, T& total, T* s_w) {
+  constexpr int NW = NT / 32;
+  static_assert(NW <= 32, "one warp scans the warp sums");
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  T incl = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(kFull, v, o);
-    if (lane >= (uint32_t)o) v += t;
+    const T t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= (uint32_t)o) incl += t;
   }
-  return v;
-}
-
-// Exclusive scan of one value per thread over a block of NT threads.
-// s_w must hold NT/32 + 1 words.  Must be called by every thread.
-template <int NT>
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total, uint32_t* s_w) {
-  constexpr int NW = NT / 32;
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  const uint32_t incl = warp_incl_scan(v);
   if (lane == 31) s_w[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    uint32_t w = lane < NW ? s_w[lane] : 0;
-    uint32_t wi = warp_incl_scan(w);
-    if (lane < NW) s_w[lane] = wi - w;
-    if (lane == NW - 1) s_w[NW] = wi;
+    const T w = lane < (uint32_t)NW ? s_w[lane] : T(0);
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T t = __shfl_up_sync(kFull, wi, o);
+      if (lane >= (uint32_t)o) wi += t;
+    }
+    if (lane < (uint32_t)NW) s_w[lane] = wi - w;
+    if (lane == (uint32_t)NW - 1) s_w[NW] = wi;
   }
   __syncthreads();
   total = s_w[NW];
-  const uint32_t out = s_w[warp] + incl - v;
+  const T out = s_w[warp] + incl - v;
   __syncthreads();
   return out;
 }
 
-// ---------------------------------------------------------------- column scan
-
-constexpr int kScT = 256, kScI = 8;
-
-// Exclusive scan down each column of a row-major [rows][cols] matrix (out
-// may equal in); one block per column; the column sums go to totals (if
-// non-null).  With n_ptr, only the first ceil(min(*n_ptr, cap) / per_row)
-// rows are scanned: the rows that can hold counts of n items.
-__global__ void __launch_bounds__(kScT) col_scan_kernel(const uint32_t* in, uint32_t* out, uint32_t rows,
-                                                        uint32_t cols, uint32_t* totals, const uint64_t* n_ptr,
-                                                        uint32_t cap, uint32_t per_row) {
-  wait_prior_grid();
-  __shared__ uint32_t s_w[kScT / 32 + 1];
-  const uint32_t c = blockIdx.x;
-  if (n_ptr) {
-    const uint64_t n = *n_ptr < cap ? *n_ptr : cap;
-    const uint64_t used = (n + per_row - 1) / per_row;
-    if (used < rows) rows = (uint32_t)used;
-  }
-  uint32_t carry = 0;
-  for (uint32_t r0 = 0; r0 < rows; r0 += kScT * kScI) {
-    uint32_t v[kScI], sum = 0;
-    const uint32_t rb = r0 + threadIdx.x * kScI;
-#pragma unroll
-    for (int i = 0; i < kScI; ++i) {
-      v[i] = (rb + i < rows) ? in[(size_t)(rb + i) * cols + c] : 0u;
-      sum += v[i];
-    }
-    uint32_t total;
-    uint32_t ex = block_excl_scan<kScT>(sum, total, s_w);
-#pragma unroll
-    for (int i = 0; i < kScI; ++i) {
-      if (rb + i < rows) out[(size_t)(rb + i) * cols + c] = carry + ex;
-      ex += v[i];
-    }
-    carry += total;
-  }
-  if (totals && threadIdx.x == 0) totals[c] = carry;
-}
-
-// ---------------------------------------------------------------- compaction
-
-constexpr int kCmpT = 256, kCmpI = kCmpTile / kCmpT;
-// depth pass blocks that kCmpTile consecutive output positions can fall in
-constexpr int kCmpSpan = (kCmpTile + kDsTile - 1) / kDsTile + 1;
-
-// The sum of v[0 .. n) over a block of NT threads (every thread calls it).
+// block_excl_scan of two values at once (the same barriers): a 64-bit and
+// a 32-bit count.  s_a / s_b must hold NT/32 + 1 values each.
 template <int NT>
-__device__ __forceinline__ uint32_t block_sum_prefix(const uint32_t* __restrict__ v, uint32_t n, uint32_t* s_w) {
-  uint32_t part = 0;
-  for (uint32_t i = threadIdx.x; i < n; i += NT) part += v[i];
-  uint32_t total;
-  block_excl_scan<NT>(part, total, s_w);
-  return total;
-}
-
-// Keeps the records with tiles_touched > 0, in record order, as (depth key,
-// record) pairs starting at the block's exclusive prefix of the visible
-// counts, and counts the first depth pass's digits per (pass block, digit)
-// into hist0.  The prefix is vis_prefix[block] (scanned by a kernel before),
-// or, where there are few compaction blocks (vis_count non-null), the sum of
-// the earlier blocks' counts, taken here: one launch fewer.
-constexpr uint32_t kFusePrefixMax = 2048;  // blocks up to which a block sums the earlier blocks' counts itself
-__global__ void __launch_bounds__(kCmpT) compact_kernel(const uint32_t* __restrict__ tiles,
-                                                        const uint32_t* __restrict__ key, uint32_t R,
-                                                        const uint32_t* __restrict__ vis_prefix,
-                                                        const uint32_t* __restrict__ vis_count,
-                                                        uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
-                                                        uint32_t* __restrict__ hist0, Header* hdr) {
-  wait_prior_grid();
-  __shared__ uint32_t s_w[kCmpT / 32 + 1];
-  const uint32_t t = blockIdx.x;
-  const uint32_t excl = vis_count ? block_sum_prefix<kCmpT>(vis_count, t, s_w) : vis_prefix[t];
-  const uint32_t base = t * kCmpTile + threadIdx.x * kCmpI;
-  bool f[kCmpI];
-  uint32_t k[kCmpI];
-  uint32_t cnt = 0;
+__device__ __forceinline__ void block_excl_scan2(unsigned long long a, uint32_t b, unsigned long long& ea, uint32_t& eb,
+                                                 unsigned long long& ta, uint32_t& tb, unsigned long long* s_a,
+                                                 uint32_t* s_b) {
+  constexpr int NW = NT / 32;
+  static_assert(NW <= 32, "one warp scans the warp sums");
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  unsigned long long ia = a;
+  uint32_t ib = b;
 #pragma unroll
-  for (int i = 0; i < kCmpI; ++i) {
-    const uint32_t idx = base + i;
-    f[i] = idx < R && __ldg(tiles + idx) > 0;
-    k[i] = f[i] ? __ldg(key + idx) : 0u;
-    cnt += f[i];
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long x = __shfl_up_sync(kFull, ia, o);
+    const uint32_t y = __shfl_up_sync(kFull, ib, o);
+    if (lane >= (uint32_t)o) ia += x, ib += y;
   }
-  uint32_t total;
-  uint32_t pos = excl + block_excl_scan<kCmpT>(cnt, total, s_w);
-  __shared__ uint32_t s_h[kCmpSpan][256];
-  for (int i = threadIdx.x; i < kCmpSpan * 256; i += kCmpT) (&s_h[0][0])[i] = 0;
+  if (lane == 31) s_a[warp] = ia, s_b[warp] = ib;
   __syncthreads();
-  const uint32_t ob0 = excl / kDsTile;
+  if (warp == 0) {
+    const unsigned long long wa = lane < (uint32_t)NW ? s_a[lane] : 0ull;
+    const uint32_t wb = lane < (uint32_t)NW ? s_b[lane] : 0u;
+    unsigned long long xa = wa;
+    uint32_t xb = wb;
 #pragma unroll
-  for (int i = 0; i < kCmpI; ++i)
-    if (f[i]) {
-      if (pos < R) {  // holds by construction (counts made by preprocess)
-        okey[pos] = k[i];
-        oval[pos] = base + i;
-        atomicAdd(&s_h[min(pos / kDsTile - ob0, (uint32_t)kCmpSpan - 1u)][k[i] & 255u], 1u);
-      }
-      ++pos;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long x = __shfl_up_sync(kFull, xa, o);
+      const uint32_t y = __shfl_up_sync(kFull, xb, o);
+      if (lane >= (uint32_t)o) xa += x, xb += y;
     }
+    if (lane < (uint32_t)NW) s_a[lane] = xa - wa, s_b[lane] = xb - wb;
+    if (lane == (uint32_t)NW - 1) s_a[NW] = xa, s_b[NW] = xb;
+  }
   __syncthreads();
-  // first depth pass: counts per (pass block, digit)
-  for (int i = threadIdx.x; i < kCmpSpan * 256; i += kCmpT) {
-    const uint32_t c = (&s_h[0][0])[i];
-    if (c) atomicAdd(hist0 + (size_t)(ob0 + i / 256) * 256 + (i & 255), c);
-  }
-  if (t == gridDim.x - 1 && threadIdx.x == 0) hdr->n_visible = excl + total;
-}
-
-// ---------------------------------------------------------------- radix pass
-
-constexpr int kOsT = 256, kOsW = kOsT / 32;
-
-// One stable pass of the LSD radix sort over the 8 bits at `shift`: local
-// ranking, placement at (exclusive prefix of ghist) + hprefix[block][digit]
-// + rank, and, while placing, the counts the following step needs:
-//   ghist:   digit totals of this pass over all n items
-//   hprefix: [blocks][256] exclusive column prefix of this pass's
-//            per-(block, digit) counts
-//   hnext:   if non-null, counts of the next pass's digit (at shift + 8) per
-//            (output block, digit)
-//   icount:  if non-null, instances (tiles_touched of each placed record)
-//            per emission block of the output
-// The counts are summed over lanes with equal (block, digit) before one
-// atomic add per group.  A block ranks TILE items.
-template <int TILE>
-__global__ void __launch_bounds__(kOsT, 5) downsweep_kernel(const uint32_t* __restrict__ kin,
-                                                         const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-                                                         uint32_t* __restrict__ vout, const uint64_t* n_ptr,
-                                                         uint32_t cap, int shift, const uint32_t* __restrict__ ghist,
-                                                         const uint32_t* __restrict__ hprefix, uint32_t* hnext,
-                                                         uint32_t* icount, const uint32_t* __restrict__ tiles_touched) {
-  wait_prior_grid();
-  constexpr int kOsI = TILE / kOsT;
-  __shared__ uint32_t s_keys[TILE];
-  __shared__ uint32_t s_vals[TILE];
-  __shared__ uint32_t s_hist[kOsW][256];
-  __shared__ uint32_t s_boff[256];
-  __shared__ uint32_t s_goff[256];
-  __shared__ uint32_t s_w[kOsT / 32 + 1];
-  const uint64_t n64 = *n_ptr;
-  const uint32_t n = (uint32_t)(n64 < cap ? n64 : cap);
-  // grid-stride over the pass's tiles (the grid is sized by the capacity,
-  // the work by the count found on the device)
-  for (uint32_t t = blockIdx.x; (uint64_t)t * TILE < n; t += gridDim.x) {
-    __syncthreads();  // the shared arrays of the previous tile are free
-    const uint32_t tile_base = t * TILE;
-    for (int i = threadIdx.x; i < kOsW * 256; i += kOsT) (&s_hist[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint32_t wbase = tile_base + warp * (kOsI * 32);
-    uint32_t k[kOsI], v[kOsI], rank[kOsI];
-#pragma unroll
-    for (int i = 0; i < kOsI; ++i) {
-      const uint32_t idx = wbase + i * 32 + lane;
-      const bool ok = idx < n;
-      k[i] = ok ? kin[idx] : 0u;
-      v[i] = ok ? vin[idx] : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < kOsI; ++i) {
-      const uint32_t idx = wbase + i * 32 + lane;
-      const bool ok = idx < n;
-      const uint32_t d = ok ? (k[i] >> shift) & 255u : 0x100u;
-      const uint32_t peers = peer_mask(d);
-      uint32_t cnt = 0;
-      if (d < 256) cnt = s_hist[warp][d];
-      __syncwarp();
-      rank[i] = ok ? cnt + __popc(peers & lt_mask) : 0xffffffffu;
-      if (d < 256 && lane == (uint32_t)(__ffs(peers) - 1)) s_hist[warp][d] = cnt + __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    const uint32_t d = threadIdx.x;  // one digit per thread
-    uint32_t acc = 0;
-#pragma unroll
-    for (int w = 0; w < kOsW; ++w) {
-      const uint32_t c = s_hist[w][d];
-      s_hist[w][d] = acc;
-      acc += c;
-    }
-    uint32_t gtot;
-    const uint32_t gbase = block_excl_scan<kOsT>(ghist[d], gtot, s_w);
-    uint32_t btot;
-    const uint32_t boff = block_excl_scan<kOsT>(acc, btot, s_w);
-    s_boff[d] = boff;
-    s_goff[d] = gbase + hprefix[(size_t)t * 256 + d] - boff;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kOsI; ++i) {
-      if (rank[i] != 0xffffffffu) {
-        const uint32_t dd = (k[i] >> shift) & 255u;
-        const uint32_t pos = s_boff[dd] + s_hist[warp][dd] + rank[i];
-        s_keys[pos] = k[i];
-        s_vals[pos] = v[i];
-      }
-    }
-    __syncthreads();
-    const uint32_t cnt_tile = (n - tile_base) < (uint32_t)TILE ? (n - tile_base) : (uint32_t)TILE;
-#pragma unroll 4
-    for (int it = 0; it < kOsI; ++it) {
-      const uint32_t j = it * kOsT + threadIdx.x;
-      bool valid = j < cnt_tile;
-      uint32_t key = 0, val = 0, g = 0;
-      if (valid) {
-        key = s_keys[j];
-        val = s_vals[j];
-        g = s_goff[(key >> shift) & 255u] + j;
-        valid = g < n;  // holds by construction (consistent digit counts)
-        if (valid) {
-          kout[g] = key;
-          vout[g] = val;
-        }
-      }
-      if (hnext) {
-        const uint32_t grp = valid ? ((g / TILE) << 8) | ((key >> (shift + 8)) & 255u) : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(kFull, grp);
-        if (valid && lane == (uint32_t)(__ffs(peers) - 1))
-          atomicAdd(hnext + (size_t)(grp >> 8) * 256 + (grp & 255u), (uint32_t)__popc(peers));
-      }
-      if (icount) {
-        const uint32_t grp = valid ? g / kEmTile : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(kFull, grp);
-        const uint32_t sum = __reduce_add_sync(peers, valid ? tiles_touched[val] : 0u);
-        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(icount + grp, sum);
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------- emission
-
-constexpr int kEmT = 256, kEmI = kEmTile / kEmT;
-
-// First instance of each depth-sorted record: ioff[i] = the block's
-// exclusive prefix of the instance counts + the exclusive scan of
-// tiles_touched within the block.  The prefix is icount[block], scanned in
-// place by a kernel before, or, with `summed` (few blocks), the sum of the
-// earlier blocks' raw counts, taken here.  The last block records the
-// instance total and flags an instance capacity overflow.
-__global__ void __launch_bounds__(kEmT) emit_offsets_kernel(const uint32_t* __restrict__ srec,
-                                                            const uint32_t* __restrict__ tiles,
-                                                            const uint32_t* __restrict__ icount, bool summed,
-                                                            uint32_t* __restrict__ ioff, uint32_t cap, Header* hdr) {
-  wait_prior_grid();
-  __shared__ uint32_t s_w[kEmT / 32 + 1];
-  __shared__ uint32_t s_pre;
-  const uint32_t n = (uint32_t)hdr->n_visible;
-  const uint32_t n_blocks = (n + kEmTile - 1) / kEmTile;
-  for (uint32_t t = blockIdx.x; t < n_blocks; t += gridDim.x) {
-    if (summed) {
-      const uint32_t pre = block_sum_prefix<kEmT>(icount, t, s_w);
-      if (threadIdx.x == 0) s_pre = pre;
-    } else if (threadIdx.x == 0) {
-      s_pre = icount[t];
-    }
-    __syncthreads();
-    const uint32_t prefix = s_pre;
-    const uint32_t base = t * kEmTile + threadIdx.x * kEmI;
-    uint32_t c[kEmI], sum = 0;
-#pragma unroll
-    for (int i = 0; i < kEmI; ++i) {
-      c[i] = base + i < n ? tiles[srec[base + i]] : 0u;
-      sum += c[i];
-    }
-    uint32_t total;
-    uint32_t ex = prefix + block_excl_scan<kEmT>(sum, total, s_w);
-#pragma unroll
-    for (int i = 0; i < kEmI; ++i) {
-      if (base + i < n) ioff[base + i] = ex;
-      ex += c[i];
-    }
-    if (t == n_blocks - 1 && threadIdx.x == 0) {
-      const uint64_t n_inst = (uint64_t)prefix + total;
-      hdr->n_inst = n_inst;
-      if (n_inst > cap) set_status(hdr, kDevCapacity);
-    }
-  }
-}
-
-constexpr int kFlT = 256, kFlI = kIsTile / kFlT;
-static_assert(kFlI == 8, "a thread's instances are written as two 16-byte vectors per array");
-static_assert(kMaxViews <= 256, "view indices are staged as bytes");
-
-// Instances [b K, (b + 1) K) of the depth-sorted order, K = kIsTile: block b
-// of the first tile-key pass, so that every block does the same work however
-// unevenly the instances fall over the records.  Instance j belongs to the
-// sorted record i with ioff[i] <= j < ioff[i + 1] and is that record's
-// (j - ioff[i])-th tile, row-major in its rectangle; it is written as
-// (global tile, record).  ioff strictly increases (every visible record
-// touches a tile), so the block's instances lie in at most K records from
-// the one holding its first instance.  The block first stages those
-// records (id, rectangle, view) in shared memory, all gathers in flight at
-// once; each thread then walks its kFlI consecutive instances from shared
-// memory and writes them as 16-byte vectors.  Writes the first tile pass's
-// digit counts of the block.
-__global__ void __launch_bounds__(kFlT) emit_fill_kernel(const uint32_t* __restrict__ srec,
-                                                         const uint32_t* __restrict__ ioff,
-                                                         const uint2* __restrict__ rect,
-                                                         const ViewDev* __restrict__ views, int V, uint32_t cap,
-                                                         uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-                                                         uint32_t* __restrict__ hist0, const Header* hdr) {
-  wait_prior_grid();
-  __shared__ uint32_t s_off[kIsTile + 1];
-  __shared__ uint32_t s_rec[kIsTile];
-  __shared__ uint2 s_rect[kIsTile];
-  __shared__ uint8_t s_view[kIsTile];
-  __shared__ uint32_t s_h[256];
-  __shared__ uint32_t s_recoff[kMaxViews], s_tileoff[kMaxViews], s_tilesx[kMaxViews];
-  __shared__ uint32_t s_r0, s_nr;
-  const uint32_t nv = (uint32_t)hdr->n_visible;
-  const uint64_t ni64 = hdr->n_inst;
-  const uint32_t n_inst = (uint32_t)(ni64 < cap ? ni64 : cap);
-  if (nv == 0) return;
-  for (int i = threadIdx.x; i < V; i += kFlT) {
-    s_recoff[i] = views[i].rec_off;
-    s_tileoff[i] = views[i].tile_off;
-    s_tilesx[i] = (uint32_t)views[i].tiles_x;
-  }
-  for (uint32_t b = blockIdx.x; (uint64_t)b * kIsTile < n_inst; b += gridDim.x) {
-    const uint32_t s = b * kIsTile;
-    __syncthreads();  // the shared arrays of the previous block are free
-    for (int i = threadIdx.x; i < 256; i += kFlT) s_h[i] = 0;
-    if (threadIdx.x == 0) s_nr = 0;
-    if (threadIdx.x < 32) {
-      // the last sorted record with ioff <= s, by a 32-way search: each round
-      // samples 32 offsets of [lo, hi) and keeps the span after the last one
-      // <= s (ioff[0] = 0 <= s, so lane 0's sample always qualifies)
-      const uint32_t lane = threadIdx.x;
-      uint32_t lo = 0, hi = nv;
-      while (hi - lo > 32) {
-        const uint32_t step = (hi - lo + 31) / 32;
-        const uint32_t idx = lo + lane * step;
-        const uint32_t m = __ballot_sync(kFull, idx < hi && ioff[idx] <= s);
-        lo += (31u - __clz(m)) * step;
-        hi = min(hi, lo + step);
-      }
-      const uint32_t idx = lo + lane;
-      const uint32_t m = __ballot_sync(kFull, idx < hi && ioff[idx] <= s);
-      if (lane == 0) s_r0 = lo + 31u - __clz(m);
-    }
-    __syncthreads();
-    const uint32_t r0 = s_r0;
-    // the offsets of records r0 .. r0 + K, and the number of those records
-    // that start inside the block (the records holding its instances)
-    uint32_t starts = 0;
-    for (uint32_t i = threadIdx.x; i <= (uint32_t)kIsTile; i += kFlT) {
-      const uint32_t o = r0 + i < nv ? ioff[r0 + i] : 0xffffffffu;
-      s_off[i] = o;
-      starts += (i < (uint32_t)kIsTile && o < s + (uint32_t)kIsTile);
-    }
-    if (starts) atomicAdd(&s_nr, starts);
-    __syncthreads();
-    const uint32_t nr = min(s_nr, (uint32_t)kIsTile);
-    // stage those records (id, rectangle and view), a thread's ids loaded
-    // together and then its rectangles
-    {
-      uint32_t rk[kFlI];
-      uint2 rc[kFlI];
-#pragma unroll
-      for (int k = 0; k < kFlI; ++k) {
-        const uint32_t i = threadIdx.x + k * kFlT;
-        rk[k] = i < nr ? srec[r0 + i] : 0u;
-      }
-#pragma unroll
-      for (int k = 0; k < kFlI; ++k) {
-        const uint32_t i = threadIdx.x + k * kFlT;
-        if (i < nr) rc[k] = rect[rk[k]];
-      }
-#pragma unroll
-      for (int k = 0; k < kFlI; ++k) {
-        const uint32_t i = threadIdx.x + k * kFlT;
-        if (i < nr) {
-          int vlo = 0, vhi = V - 1;  // view of the record: last view with rec_off <= rec
-          while (vlo < vhi) {
-            const int mid = (vlo + vhi + 1) >> 1;
-            if (s_recoff[mid] <= rk[k]) vlo = mid; else vhi = mid - 1;
-          }
-          s_rec[i] = rk[k];
-          s_rect[i] = rc[k];
-          s_view[i] = (uint8_t)vlo;
-        }
-      }
-    }
-    __syncthreads();
-    // kFlI consecutive instances per thread, walking the staged records
-    const uint32_t j0 = s + threadIdx.x * kFlI;
-    if (j0 < n_inst) {
-      int lo = 0, hi = (int)nr - 1;  // last i with s_off[i] <= j0 (s_off[0] <= s)
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= j0) lo = mid; else hi = mid - 1;
-      }
-      uint32_t i = (uint32_t)lo;
-      uint32_t kk[kFlI], vv[kFlI];
-      uint32_t rec = 0, x0 = 0, x1 = 0, tx = 0, ty = 0, vt = 0, vx = 0;
-      bool fresh = true;
-#pragma unroll
-      for (int k = 0; k < kFlI; ++k) {
-        const uint32_t j = j0 + k;
-        kk[k] = vv[k] = 0;
-        if (j < n_inst) {
-          while (s_off[i + 1] <= j) {  // stays below nr: s_off[nr] > j
-            ++i;
-            fresh = true;
-          }
-          if (fresh) {
-            fresh = false;
-            rec = s_rec[i];
-            const uint2 rc = s_rect[i];
-            x0 = rc.x & 0xFFFFu;
-            x1 = rc.y & 0xFFFFu;
-            const uint32_t w = x1 - x0, local = j - s_off[i];
-            tx = x0 + local % w;
-            ty = (rc.x >> 16) + local / w;
-            vt = s_tileoff[s_view[i]];
-            vx = s_tilesx[s_view[i]];
-          }
-          const uint32_t gt = vt + ty * vx + tx;
-          kk[k] = gt;
-          vv[k] = rec;
-          atomicAdd(&s_h[gt & 255u], 1u);
-          if (++tx == x1) {
-            tx = x0;
-            ++ty;
-          }
-        }
-      }
-      if (j0 + kFlI <= n_inst) {  // j0 is a multiple of 8: 32-byte aligned
-        uint4* kd = reinterpret_cast<uint4*>(ikey + j0);
-        uint4* vd = reinterpret_cast<uint4*>(ival + j0);
-        kd[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
-        kd[1] = make_uint4(kk[4], kk[5], kk[6], kk[7]);
-        vd[0] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
-        vd[1] = make_uint4(vv[4], vv[5], vv[6], vv[7]);
-      } else {
-#pragma unroll
-        for (int k = 0; k < kFlI; ++k)
-          if (j0 + k < n_inst) {
-            ikey[j0 + k] = kk[k];
-            ival[j0 + k] = vv[k];
-          }
-      }
-    }
-    __syncthreads();
-    // this block is block b of the first tile pass: its counts are
-    // written whole (no pass and no counts when the problem has one tile)
-    if (hist0)
-      for (int d = threadIdx.x; d < 256; d += kFlT) hist0[(size_t)b * 256 + d] = s_h[d];
-  }
-}
-
-// ---------------------------------------------------------------- ranges
-
-// Position i of the sorted tile keys starts the ranges of every tile g with
-// key[i-1] < g <= key[i] (key[-1] = -1, key[n] = NT), so tstart[g] is the
-// first position whose key is >= g, and tstart[NT] = n.
-__global__ void ranges_kernel(const uint32_t* __restrict__ skeys, const uint64_t* n_ptr, uint32_t cap, uint32_t NT,
-                              uint32_t* __restrict__ tstart) {
-  wait_prior_grid();
-  const uint64_t n64 = *n_ptr;
-  const uint32_t n = (uint32_t)(n64 < cap ? n64 : cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
-    const int64_t prev = i > 0 ? (int64_t)skeys[i - 1] : -1;
-    const int64_t cur = i < n ? (int64_t)min(skeys[i], NT) : (int64_t)NT;
-    for (int64_t g = prev + 1; g <= cur; ++g) tstart[g] = i;
-  }
+  ta = s_a[NW];
+  tb = s_b[NW];
+  ea = s_a[warp] + ia - a;
+  eb = s_b[warp] + ib - b;
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- tile order
@@ -585,217 +151,711 @@ __device__ __forceinline__ uint32_t bucket_add(uint32_t* s, int b) {
   return base + __popc(peers & ((1u << lane) - 1u));
 }
 
-// The tiles in the order the blend kernels take them.  Where lists are long
-// on average, by list length, longest first (to a quarter octave; the order
-// within a bucket is arbitrary), so that long tiles start early and do not
-// trail the grid; where they are short, the blend kernels keep the tiles'
-// own order (neighbouring tiles share records) and nothing here runs.
-// Every tile appears once, so the order changes no result.
-//
-// Up to kOrdSingle tiles: one block counts the tiles per bucket, scans the
-// counts and places the tiles.
-constexpr uint32_t kOrdSingle = 16384;
-__global__ void __launch_bounds__(kOrdT) tile_order_single_kernel(const uint32_t* __restrict__ tstart, uint32_t NT,
-                                                                 uint32_t cap, const Header* hdr,
-                                                                 uint32_t* __restrict__ order) {
-  wait_prior_grid();
-  if (!order_dense(hdr, NT, cap)) return;
-  __shared__ uint32_t s_n[kOrdBuckets];
-  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT) s_n[i] = 0;
+// ---------------------------------------------------------------- scan
+
+// Places each thread's item (bucket b, or none if b < 0) of this block in
+// the bucket order: bucket i's range starts after the totals of the buckets
+// before it (totals, complete over every block), and each block takes its
+// part of that range from the bucket's cursor.  Returns the position, ~0
+// where b < 0.  Block-uniform call (every thread).
+template <int NT>
+__device__ __forceinline__ uint32_t bucket_place(const uint32_t* __restrict__ totals, uint32_t* __restrict__ cursors,
+                                                 int b, uint32_t* s_n, uint32_t* s_base) {
+  for (int i = threadIdx.x; i < kOrdBuckets; i += NT) s_n[i] = 0;
   __syncthreads();
-  // every tile's bucket in registers first: the loads are all in flight at once
-  constexpr int PER_T = kOrdSingle / kOrdT;
-  int bk[PER_T];
-#pragma unroll
-  for (int k = 0; k < PER_T; ++k) {
-    const uint32_t t = k * kOrdT + threadIdx.x;
-    bk[k] = t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1;
-  }
-#pragma unroll
-  for (int k = 0; k < PER_T; ++k)
-    if (k * kOrdT < NT) bucket_add(s_n, bk[k]);  // uniform over the block: whole warps
+  const uint32_t rank = bucket_add(s_n, b);
   __syncthreads();
-  if (threadIdx.x < 32) {  // exclusive scan of the counts: five buckets a lane
+  if (threadIdx.x < 32) {  // five buckets a lane
     constexpr int PER = (kOrdBuckets + 31) / 32;
-    const int lane = threadIdx.x;
-    uint32_t c[PER], sum = 0;
+    const uint32_t lane = threadIdx.x;
+    uint32_t tot[PER], sum = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-      const int i = lane * PER + j;
-      c[j] = i < kOrdBuckets ? s_n[i] : 0u;
-      sum += c[j];
+      const uint32_t i = lane * PER + j;
+      tot[j] = i < (uint32_t)kOrdBuckets ? totals[i] : 0u;
+      sum += tot[j];
     }
     uint32_t incl = sum;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += o;
+      const uint32_t o = __shfl_up_sync(kFull, incl, d);
+      if (lane >= (uint32_t)d) incl += o;
     }
-    uint32_t run = incl - sum;
+    uint32_t start = incl - sum;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-      const int i = lane * PER + j;
-      if (i < kOrdBuckets) s_n[i] = run;
-      run += c[j];
+      const uint32_t i = lane * PER + j;
+      if (i < (uint32_t)kOrdBuckets && s_n[i]) s_base[i] = start + atomicAdd(cursors + i, s_n[i]);
+      start += tot[j];
     }
   }
   __syncthreads();
+  return b >= 0 ? s_base[b] + rank : ~0u;
+}
+
+
+// The tiles in the order the blend kernels take them.  Where lists are long
+// on average, by list length, longest first (to a quarter octave; the order
+// within a bucket is arbitrary), so that long tiles start early and do not
+// trail the grid; where they are short, the blend kernels keep the tiles'
+// own order (neighbouring tiles share records) and no order is made.
+// Every tile appears once, so the order changes no result.  The scan makes
+// it: its first pass counts the tiles per length bucket, its last places
+// each block's tiles after the longer buckets' totals.
+//
+// One thread per tile; kScanTiles tiles per block.
+constexpr int kScT = kScanTiles;
+static_assert(kScT == 1024, "one thread per tile");
+
+__device__ __forceinline__ uint32_t sort_items(uint32_t n) { return (n + kSortChunk - 1) / kSortChunk; }
+
+// The counts of tile t (zero past the last tile) and their sum: sub-bucket
+// u of tile t is tcount[u NT + t].
+__device__ __forceinline__ uint32_t load_tile_counts(const uint32_t* __restrict__ tcount, uint32_t t, uint32_t NT,
+                                                     uint32_t (&c)[kTileSub]) {
 #pragma unroll
-  for (int k = 0; k < PER_T; ++k)
-    if (k * kOrdT < NT) {
-      const uint32_t pos = bucket_add(s_n, bk[k]);
-      if (bk[k] >= 0) order[pos] = k * kOrdT + threadIdx.x;
-    }
+  for (int i = 0; i < (int)kTileSub; ++i) c[i] = t < NT ? tcount[(size_t)i * NT + t] : 0u;
+  uint32_t n = 0;
+#pragma unroll
+  for (int i = 0; i < (int)kTileSub; ++i) n += c[i];
+  return n;
 }
 
-// More tiles, pass 1: the tiles per bucket, one block per kOrdT tiles.
-__global__ void __launch_bounds__(kOrdT) tile_order_count_kernel(const uint32_t* __restrict__ tstart, uint32_t NT,
-                                                                uint32_t cap, const Header* hdr,
-                                                                uint32_t* __restrict__ totals) {
+// per scan block: instances (u64), chunk items of long lists, short lists
+struct ScanPart {
+  unsigned long long inst;
+  uint32_t n_long, n_short;
+};
+
+// Pass 1: each block's sums; the short lists per length bucket (the sort
+// items of short lists are placed longest first); and, with `order`, the
+// tiles per length bucket of the tile order.  The bucket counts go to
+// order_count: [0, 132) tiles, [264, 396) short lists.
+__global__ void __launch_bounds__(kScT) scan_part_kernel(const uint32_t* __restrict__ tcount, uint32_t NT,
+                                                         ScanPart* __restrict__ part,
+                                                         uint32_t* __restrict__ order_count, bool order) {
   wait_prior_grid();
-  if (!order_dense(hdr, NT, cap)) return;
-  __shared__ uint32_t s_n[kOrdBuckets];
-  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT) s_n[i] = 0;
+  __shared__ unsigned long long s_w64[kScT / 32 + 1];
+  __shared__ uint32_t s_w[kScT / 32 + 1];
+  __shared__ uint32_t s_n[2][kOrdBuckets];
+  const uint32_t t = blockIdx.x * kScT + threadIdx.x;
+  uint32_t c[kTileSub];
+  const uint32_t n = load_tile_counts(tcount, t, NT, c);
+  for (int i = threadIdx.x; i < 2 * kOrdBuckets; i += kScT) (&s_n[0][0])[i] = 0;
   __syncthreads();
-  const uint32_t t = blockIdx.x * kOrdT + threadIdx.x;
-  bucket_add(s_n, t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1);
+  bucket_add(s_n[1], t < NT && n > 0 && n <= kSortChunk ? length_bucket(n) : -1);
+  if (order) bucket_add(s_n[0], t < NT ? length_bucket(n) : -1);
   __syncthreads();
-  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT)
-    if (s_n[i]) atomicAdd(totals + i, s_n[i]);
+  for (int i = threadIdx.x; i < 2 * kOrdBuckets; i += kScT) {
+    const uint32_t v = (&s_n[0][0])[i];
+    if (v) atomicAdd(order_count + (i < kOrdBuckets ? i : 2 * kOrdBuckets + (i - kOrdBuckets)), v);
+  }
+  unsigned long long ea, ti;
+  uint32_t es, ts, tl;
+  block_excl_scan2<kScT>((unsigned long long)n, n > 0 && n <= kSortChunk ? 1u : 0u, ea, es, ti, ts, s_w64, s_w);
+  block_excl_scan<uint32_t, kScT>(n > kSortChunk ? sort_items(n) : 0u, tl, s_w);
+  if (threadIdx.x == 0) part[blockIdx.x] = ScanPart{ti, tl, ts};
 }
 
-// Pass 2: each block reserves a range per bucket (after the longer buckets'
-// totals) and places its tiles there.
-__global__ void __launch_bounds__(kOrdT) tile_order_place_kernel(const uint32_t* __restrict__ tstart, uint32_t NT,
-                                                                uint32_t cap, const Header* hdr,
-                                                                const uint32_t* __restrict__ totals,
-                                                                uint32_t* __restrict__ cursor,
-                                                                uint32_t* __restrict__ order) {
+// Pass 2 (one block; only where there are more than kFusePrefixMax scan
+// blocks): every block's exclusive prefix and the totals.
+constexpr uint32_t kFusePrefixMax = 2048;  // blocks up to which the last pass sums the earlier blocks' parts itself
+__global__ void __launch_bounds__(kScT) scan_mid_kernel(const ScanPart* __restrict__ part, uint32_t nb,
+                                                        ScanPart* __restrict__ pre, ScanPart* __restrict__ tot) {
   wait_prior_grid();
-  if (!order_dense(hdr, NT, cap)) return;
-  const uint32_t t = blockIdx.x * kOrdT + threadIdx.x;
+  __shared__ unsigned long long s_w64[kScT / 32 + 1];
+  __shared__ uint32_t s_w[kScT / 32 + 1];
+  ScanPart carry{0ull, 0u, 0u};
+  for (uint32_t b0 = 0; b0 < nb; b0 += kScT) {
+    const uint32_t b = b0 + threadIdx.x;
+    const ScanPart v = b < nb ? part[b] : ScanPart{0ull, 0u, 0u};
+    unsigned long long ti;
+    uint32_t tl, ts;
+    const unsigned long long ei = block_excl_scan<unsigned long long, kScT>(v.inst, ti, s_w64);
+    const uint32_t el = block_excl_scan<uint32_t, kScT>(v.n_long, tl, s_w);
+    const uint32_t es = block_excl_scan<uint32_t, kScT>(v.n_short, ts, s_w);
+    if (b < nb) pre[b] = ScanPart{carry.inst + ei, carry.n_long + el, carry.n_short + es};
+    carry.inst += ti;
+    carry.n_long += tl;
+    carry.n_short += ts;
+  }
+  if (threadIdx.x == 0) *tot = carry;
+}
+
+// The last pass: each tile's range and sub-bucket cursors, the sort items
+// (every chunk of a long list first, then one per short list) and the tile
+// order.  With few blocks (pre null) a block sums the earlier blocks' parts
+// itself; else it reads the prefixes and totals of scan_mid_kernel.  Block
+// 0 records the totals (and a capacity overflow, after which every list is
+// empty and there is no item).
+__global__ void __launch_bounds__(kScT) scan_place_kernel(const uint32_t* __restrict__ tcount, uint32_t NT,
+                                                          uint32_t cap, const ScanPart* __restrict__ part, uint32_t nb,
+                                                          const ScanPart* __restrict__ pre,
+                                                          const ScanPart* __restrict__ tot, Header* hdr,
+                                                          uint32_t* __restrict__ tstart,
+                                                          uint32_t* __restrict__ cursor, uint2* __restrict__ items,
+                                                          uint32_t* __restrict__ order_count,
+                                                          uint32_t* __restrict__ order) {
+  wait_prior_grid();
+  __shared__ unsigned long long s_w64[kScT / 32 + 1];
+  __shared__ uint32_t s_w[kScT / 32 + 1];
   __shared__ uint32_t s_n[kOrdBuckets], s_base[kOrdBuckets];
-  for (int i = threadIdx.x; i < kOrdBuckets; i += kOrdT) s_n[i] = 0;
-  __syncthreads();
-  const int b = t < NT ? length_bucket(tstart[t + 1] - tstart[t]) : -1;
-  const uint32_t rank = bucket_add(s_n, b);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t start = 0;  // the bucket's first position: the longer buckets' totals
-    for (int i = 0; i < kOrdBuckets; ++i) {
-      if (s_n[i]) s_base[i] = start + atomicAdd(cursor + i, s_n[i]);
-      start += totals[i];
+  __shared__ ScanPart s_pt[2];
+  if (threadIdx.x < 32) {
+    // the parts before this block (P) and of all blocks (T): one warp
+    ScanPart P{0ull, 0u, 0u}, T{0ull, 0u, 0u};
+    if (pre) {
+      P = pre[blockIdx.x];
+      T = *tot;
+    } else {
+      for (uint32_t b = threadIdx.x; b < nb; b += 32) {
+        const ScanPart v = part[b];
+        if (b < blockIdx.x) P.inst += v.inst, P.n_long += v.n_long, P.n_short += v.n_short;
+        T.inst += v.inst, T.n_long += v.n_long, T.n_short += v.n_short;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        P.inst += __shfl_xor_sync(kFull, P.inst, o);
+        P.n_long += __shfl_xor_sync(kFull, P.n_long, o);
+        P.n_short += __shfl_xor_sync(kFull, P.n_short, o);
+        T.inst += __shfl_xor_sync(kFull, T.inst, o);
+        T.n_long += __shfl_xor_sync(kFull, T.n_long, o);
+        T.n_short += __shfl_xor_sync(kFull, T.n_short, o);
+      }
     }
+    if (threadIdx.x == 0) s_pt[0] = P, s_pt[1] = T;
   }
   __syncthreads();
-  if (b >= 0) order[s_base[b] + rank] = t;
+  const ScanPart P = s_pt[0], T = s_pt[1];
+  const bool over = T.inst > cap;
+  const uint32_t t = blockIdx.x * kScT + threadIdx.x;
+  uint32_t c[kTileSub];
+  const uint32_t n = load_tile_counts(tcount, t, NT, c);
+  const uint32_t nl = n > kSortChunk ? sort_items(n) : 0u;
+  unsigned long long ei, bi;
+  uint32_t el, bl;
+  block_excl_scan2<kScT>((unsigned long long)n, nl, ei, el, bi, bl, s_w64, s_w);
+  // the short lists' items, after every long list's chunks, longest first
+  const bool is_short = t < NT && n > 0 && n <= kSortChunk;
+  const uint32_t ps = bucket_place<kScT>(order_count + 2 * kOrdBuckets, order_count + 3 * kOrdBuckets,
+                                         is_short ? length_bucket(n) : -1, s_n, s_base);
+  if (t < NT) {
+    uint32_t run = over ? 0u : (uint32_t)(P.inst + ei);
+    tstart[t] = run;
+#pragma unroll
+    for (int i = 0; i < (int)kTileSub; ++i) {
+      cursor[(size_t)i * NT + t] = run;
+      if (!over) run += c[i];
+    }
+    if (!over) {
+      const uint32_t l0 = P.n_long + el;
+      for (uint32_t ch = 0; ch < nl; ++ch) items[l0 + ch] = make_uint2(t, ch);
+      if (is_short && ps < T.n_short) items[T.n_long + ps] = make_uint2(t, 0u);  // ps < n_short holds
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hdr->ctr[kCtrSortItems] = 0;  // the per-tile sort's item counter
+    tstart[NT] = over ? 0u : (uint32_t)T.inst;
+    hdr->n_inst = T.inst;
+    hdr->n_long = over ? 0u : T.n_long;
+    hdr->n_items = over ? 0u : T.n_long + T.n_short;
+    if (over) set_status(hdr, kDevCapacity);
+  }
+  if (order && !over && T.inst >= (unsigned long long)kOrdDense * NT) {  // uniform over the block
+    const uint32_t pos = bucket_place<kScT>(order_count, order_count + kOrdBuckets, t < NT ? length_bucket(n) : -1,
+                                            s_n, s_base);
+    if (t < NT && pos < NT) order[pos] = t;  // pos < NT holds: the totals count every tile
+  }
+}
+
+// ---------------------------------------------------------------- count and scatter
+
+constexpr int kScatT = 256, kScatW = kScatT / 32;
+
+// The view constants the walk over the visibility masks needs, per block.
+struct ViewTable {
+  uint32_t recoff[kMaxViews], maskoff[kMaxViews], toff[kMaxViews], tsx[kMaxViews];
+};
+
+__device__ __forceinline__ void stage_views(ViewTable& t, const ViewDev* __restrict__ views, int V) {
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    t.recoff[i] = views[i].rec_off;
+    t.maskoff[i] = views[i].mask_off;
+    t.toff[i] = views[i].tile_off;
+    t.tsx[i] = (uint32_t)views[i].tiles_x;
+  }
+}
+
+// Walks the visible records (the set bits of the visibility masks): each
+// warp takes chunks of `chunk` (<= 32) consecutive mask words, a grid-
+// stride loop over the chunks, loads the chunk's words together (one a
+// lane), lists the records of their set bits in shared memory and then
+// calls f(r, n, rc, toff, tsx) for 32 of them at a time, one a lane: record
+// r, its tile count n (0 on the lanes past the list's end, which load
+// nothing), its rectangle rc and its view's first tile and tiles per row.
+// Every lane of the warp calls f together.  s_list holds 32 x 32 entries
+// per warp.
+template <class F>
+__device__ __forceinline__ void walk_visible(const uint32_t* __restrict__ vis_mask, uint32_t mask_words,
+                                             uint32_t chunk, const ViewTable& vt, int V,
+                                             const uint32_t* __restrict__ tiles, const uint2* __restrict__ rect,
+                                             uint32_t* s_list, F&& f) {
+  const uint32_t lane = lane_id();
+  const uint32_t n_chunks = (mask_words + chunk - 1) / chunk;
+  const uint32_t nw = gridDim.x * kScatW;
+  for (uint32_t c = blockIdx.x * kScatW + (threadIdx.x >> 5); c < n_chunks; c += nw) {
+    const uint32_t word = c * chunk + lane;
+    const uint32_t m = (lane < chunk && word < mask_words) ? vis_mask[word] : 0u;
+    const uint32_t cnt = __popc(m);
+    uint32_t off = cnt;  // inclusive scan of the counts over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, off, o);
+      if (lane >= (uint32_t)o) off += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, off, 31);
+    if (total == 0) continue;
+    if (m) {
+      int lo = 0, hi = V - 1;  // the word's view: the last with mask_off <= word
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vt.maskoff[mid] <= word) lo = mid; else hi = mid - 1;
+      }
+      const uint32_t r0 = vt.recoff[lo] + (word - vt.maskoff[lo]) * 32;
+      uint32_t at = off - cnt;
+      for (uint32_t b = m; b; b &= b - 1) s_list[at++] = r0 + (uint32_t)(__ffs(b) - 1);
+    }
+    __syncwarp();
+    for (uint32_t g = 0; g < total; g += 32) {  // warp-uniform
+      const bool on = g + lane < total;
+      const uint32_t r = on ? s_list[g + lane] : 0u;
+      const uint32_t n = on ? tiles[r] : 0u;
+      const uint2 rc = on ? rect[r] : make_uint2(0u, 0u);
+      uint32_t toff = 0, tsx = 0;
+      if (on) {
+        int lo = 0, hi = V - 1;  // the record's view: the last with rec_off <= r
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (vt.recoff[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        toff = vt.toff[lo];
+        tsx = vt.tsx[lo];
+      }
+      f(r, n, rc, toff, tsx);
+    }
+    __syncwarp();  // the list is read before the next chunk's is written
+  }
+}
+
+// B1: every visible record adds one to its sub-bucket (record index mod
+// kTileSub) of each tile of its rectangle, and the visible records are
+// summed into 32 partial sums (global warp id mod 32, 128 bytes apart).
+__global__ void __launch_bounds__(kScatT) count_kernel(const uint32_t* __restrict__ tiles,
+                                                       const uint2* __restrict__ rect,
+                                                       const uint32_t* __restrict__ vis_mask, uint32_t mask_words,
+                                                       uint32_t chunk, const ViewDev* __restrict__ views, int V,
+                                                       uint32_t NT, uint32_t* __restrict__ tcount,
+                                                       uint32_t* __restrict__ vis_part) {
+  wait_prior_grid();
+  __shared__ ViewTable s_vt;
+  __shared__ uint32_t s_list[kScatW][32 * 32];
+  stage_views(s_vt, views, V);
+  __syncthreads();
+  uint32_t nvis = 0;
+  walk_visible(vis_mask, mask_words, chunk, s_vt, V, tiles, rect, s_list[threadIdx.x >> 5],
+               [&](uint32_t r, uint32_t n, uint2 rc, uint32_t toff, uint32_t tsx) {
+                 nvis += n != 0;
+                 uint32_t* sub = tcount + (r & (kTileSub - 1)) * NT + toff;
+                 if (n != 0 && n <= kSoloTiles) {
+                   const uint32_t x0 = rc.x & 0xFFFFu, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
+                   for (uint32_t ty = rc.x >> 16; ty < y1; ++ty)
+                     for (uint32_t tx = x0; tx < x1; ++tx)
+                       if (toff + ty * tsx + tx < NT) atomicAdd(sub + ty * tsx + tx, 1u);  // holds: in the view
+                 }
+                 walk_large_rects(n, rc, toff, tsx, r, [&](uint32_t g, uint32_t rec) {
+                   if (g < NT) atomicAdd(tcount + (rec & (kTileSub - 1)) * NT + g, 1u);
+                 });
+               });
+  const uint32_t w = __reduce_add_sync(kFull, nvis);
+  if (lane_id() == 0 && w) atomicAdd(vis_part + 32 * ((blockIdx.x * kScatW + (threadIdx.x >> 5)) & 31u), w);
+}
+
+// Every visible record writes its index into the bucket of each tile of its
+// rectangle, at a slot taken from its sub-bucket's cursor: a lane's own
+// rectangle of up to kSoloTiles tiles with all its adds in flight together,
+// a larger one with all lanes of the warp working on it in turn.  Nothing is
+// written after a capacity overflow.  Block 0 also zeroes the length
+// buckets' totals and cursors, which the scan has used, for the next
+// binning on this workspace.
+__global__ void __launch_bounds__(kScatT) scatter_kernel(const uint32_t* __restrict__ tiles,
+                                                         const uint2* __restrict__ rect,
+                                                         const uint32_t* __restrict__ vis_mask, uint32_t mask_words,
+                                                         uint32_t chunk, const ViewDev* __restrict__ views, int V,
+                                                         uint32_t NT, uint32_t cap, const Header* hdr,
+                                                         uint32_t* cursor, uint32_t* __restrict__ bucket,
+                                                         uint32_t* __restrict__ order_count) {
+  wait_prior_grid();
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < 4 * kOrdBuckets; i += kScatT) order_count[i] = 0;
+  __shared__ ViewTable s_vt;
+  __shared__ uint32_t s_list[kScatW][32 * 32];
+  stage_views(s_vt, views, V);
+  __syncthreads();
+  if (hdr->n_inst > cap) return;
+  walk_visible(vis_mask, mask_words, chunk, s_vt, V, tiles, rect, s_list[threadIdx.x >> 5],
+               [&](uint32_t r, uint32_t n, uint2 rc, uint32_t toff, uint32_t tsx) {
+                 uint32_t* cur = cursor + (r & (kTileSub - 1)) * NT;
+                 if (n != 0 && n <= kSoloTiles) {
+                   uint32_t g[kSoloTiles], pos[kSoloTiles];
+                   solo_tiles(n, rc, toff, tsx, g);
+#pragma unroll
+                   for (uint32_t k = 0; k < kSoloTiles; ++k)  // g < NT holds: rectangles lie in their view
+                     pos[k] = (k < n && g[k] < NT) ? atomicAdd(cur + g[k], 1u) : cap;
+#pragma unroll
+                   for (uint32_t k = 0; k < kSoloTiles; ++k)
+                     if (pos[k] < cap) bucket[pos[k]] = r;  // holds: the counts fit the capacity
+                 }
+                 walk_large_rects(n, rc, toff, tsx, r, [&](uint32_t g, uint32_t rec) {
+                   if (g >= NT) return;
+                   const uint32_t pos = atomicAdd(cursor + (rec & (kTileSub - 1)) * NT + g, 1u);
+                   if (pos < cap) bucket[pos] = rec;
+                 });
+               });
+}
+
+// ---------------------------------------------------------------- per-tile sort
+
+// A compare-exchange of two keys: afterwards a <= b if asc, else a >= b.
+__device__ __forceinline__ void cmp_swap(unsigned long long& a, unsigned long long& b, bool asc) {
+  const bool sw = (a > b) == asc;
+  const unsigned long long lo = sw ? b : a;
+  b = sw ? a : b;
+  a = lo;
+}
+
+// Sorts a lane's K registers: ascending if asc, else descending (a static
+// bitonic network; only the last level's direction is chosen at run time).
+template <int K>
+__device__ __forceinline__ void lane_sort(unsigned long long (&v)[K], bool asc) {
+#pragma unroll
+  for (int sz = 2; sz <= K; sz <<= 1)
+#pragma unroll
+    for (int j = sz >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if ((k & j) == 0) cmp_swap(v[k], v[k | j], sz == K ? asc : (k & sz) == 0);
+}
+
+// The in-lane steps of a bitonic merge (distances K/2 .. 1), direction asc.
+template <int K>
+__device__ __forceinline__ void lane_merge(unsigned long long (&v)[K], bool asc) {
+#pragma unroll
+  for (int j = K >> 1; j > 0; j >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if ((k & j) == 0) cmp_swap(v[k], v[k | j], asc);
+}
+
+// One warp sorts the 32 K keys it holds, lane l holding positions
+// l K .. l K + K - 1, ascending by position: a bitonic sort whose blocks of
+// up to K positions are sorted inside each lane; each later round (blocks
+// of 2K .. 32K positions, direction by the block's position bit) pairs lane
+// l with lane l ^ (distance / K) by shuffles for the distances of K and
+// more, then finishes in the lane's registers.  The rounds are a loop, so
+// the code holds one copy of each step.
+template <int K>
+__device__ __forceinline__ void warp_sort_keys(unsigned long long (&v)[K]) {
+  const uint32_t lane = lane_id();
+  lane_sort<K>(v, (lane & 1u) == 0);
+#pragma unroll 1
+  for (uint32_t size = 2 * K; size <= 32 * K; size <<= 1) {
+    const bool asc = ((lane * K) & size) == 0;
+#pragma unroll 1
+    for (uint32_t lm = size / (2 * K); lm > 0; lm >>= 1) {
+      const bool keep_min = asc != ((lane & lm) != 0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const unsigned long long p = __shfl_xor_sync(kFull, v[k], lm);
+        v[k] = ((p < v[k]) == keep_min) ? p : v[k];
+      }
+    }
+    lane_merge<K>(v, asc);
+  }
+}
+
+// Sorts n <= 32 K entries of a bucket by (depth bits << 32 | record) and
+// writes the records (out32) or the keys (out64) in order; padding is ~0.
+template <int K>
+__device__ __forceinline__ void warp_sort_list(const uint32_t* __restrict__ src, uint32_t n,
+                                               const uint32_t* __restrict__ key, uint32_t R,
+                                               uint32_t* __restrict__ out32, unsigned long long* __restrict__ out64) {
+  const uint32_t lane = lane_id();
+  unsigned long long v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {  // the records first, all loads in flight, then their depth keys
+    const uint32_t i = lane * K + k;
+    v[k] = i < n ? src[i] : ~0ull;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)  // r < R holds: written by the scatter
+    if (v[k] != ~0ull) v[k] |= (unsigned long long)__ldg(key + min((uint32_t)v[k], R - 1)) << 32;
+  warp_sort_keys<K>(v);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t i = lane * K + k;
+    if (i < n) {
+      if (out32) out32[i] = (uint32_t)v[k];
+      else out64[i] = v[k];
+    }
+  }
+}
+
+constexpr int kTsW = 4;  // warps per CTA of the per-tile sort
+static_assert(kSortChunk == 32 * 32, "the widest warp sort holds 32 keys a lane");
+
+// One warp per work item, taken in order from a counter: a list of at most
+// kSortChunk entries is sorted
+// from its bucket into the instance lists; a chunk of a longer list into
+// chunk64 as keys, for the merge.  The warp takes the narrowest network
+// that holds the entries (2, 8, 16 or 32 a lane).
+__global__ void __launch_bounds__(kTsW * 32, 5) tile_sort_kernel(const uint2* __restrict__ items,
+                                                              const uint32_t* __restrict__ tstart,
+                                                              const uint32_t* __restrict__ key, uint32_t R,
+                                                              const uint32_t* __restrict__ bucket,
+                                                              uint32_t* __restrict__ out,
+                                                              unsigned long long* __restrict__ chunk64,
+                                                              Header* hdr) {
+  wait_prior_grid();
+  const uint32_t n_items = hdr->n_items;
+  for (;;) {
+    // the next item, taken from the counter (the long lists' chunks first,
+    // then the short lists longest first)
+    uint32_t it = 0;
+    if (lane_id() == 0) it = atomicAdd(&hdr->ctr[kCtrSortItems], 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= n_items) break;
+    const uint2 item = items[it];
+    const uint32_t s = tstart[item.x], e = tstart[item.x + 1];
+    const bool whole = e - s <= kSortChunk;
+    const uint32_t base = whole ? s : s + item.y * kSortChunk;
+    const uint32_t n = whole ? e - s : min(kSortChunk, e - base);
+    uint32_t* o32 = whole ? out + base : nullptr;
+    unsigned long long* o64 = whole ? nullptr : chunk64 + base;
+    if (n <= 64) warp_sort_list<2>(bucket + base, n, key, R, o32, o64);
+    else if (n <= 256) warp_sort_list<8>(bucket + base, n, key, R, o32, o64);
+    else if (n <= 512) warp_sort_list<16>(bucket + base, n, key, R, o32, o64);
+    else warp_sort_list<32>(bucket + base, n, key, R, o32, o64);
+  }
+}
+
+// ---------------------------------------------------------------- merge
+
+constexpr int kMgT = 512;  // threads of a merge CTA
+
+// The first position p in [lo, hi) of the sorted keys a[] with a[p] >= x
+// (hi if none).
+__device__ __forceinline__ uint32_t lower_bound64(const unsigned long long* __restrict__ a, uint32_t lo, uint32_t hi,
+                                                  unsigned long long x) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Merges the sorted runs A = src[a0, a0 + na) and B = src[b0, b0 + nb)
+// (distinct keys) into dst[o0, o0 + na + nb), writing only the outputs
+// [d0, d1) of the merged order: the split of output d0 between A and B is
+// found by bisection (the count i of A's keys among the first d0 outputs
+// is the one with A[i - 1] < B[d0 - i] and B[d0 - i - 1] < A[i]), then the
+// outputs are taken in order.
+__device__ __forceinline__ void merge_path(const unsigned long long* __restrict__ src, uint32_t a0, uint32_t na,
+                                           uint32_t b0, uint32_t nb, unsigned long long* __restrict__ dst,
+                                           uint32_t o0, uint32_t d0, uint32_t d1) {
+  uint32_t lo = d0 > nb ? d0 - nb : 0u, hi = d0 < na ? d0 : na;
+  while (lo < hi) {  // the smallest i with A[i] > B[d0 - i - 1]
+    const uint32_t i = (lo + hi) >> 1;
+    if (src[a0 + i] < src[b0 + (d0 - i - 1)]) lo = i + 1; else hi = i;
+  }
+  uint32_t i = lo, j = d0 - lo;
+  unsigned long long x = i < na ? src[a0 + i] : ~0ull, y = j < nb ? src[b0 + j] : ~0ull;
+  for (uint32_t d = d0; d < d1; ++d) {
+    if (x < y) {
+      dst[o0 + d] = x;
+      ++i;
+      x = i < na ? src[a0 + i] : ~0ull;
+    } else {
+      dst[o0 + d] = y;
+      ++j;
+      y = j < nb ? src[b0 + j] : ~0ull;
+    }
+  }
+}
+
+// Sorts one segment of up to kMergeSeg entries of a long list: its sorted
+// kSortChunk-runs (src[0, n)) are staged in shared memory and merged
+// pairwise in rounds; in each round every thread computes its share of the
+// outputs (kMergePer consecutive positions, found by merge path) into
+// registers, and writes them back after a barrier.  Leaves the sorted
+// segment in s_seg.  Block-uniform call.
+constexpr uint32_t kMergeSeg = 4096;
+constexpr int kMergePer = kMergeSeg / kMgT;
+__device__ __forceinline__ void merge_segment(const unsigned long long* __restrict__ src, uint32_t n,
+                                              unsigned long long* s_seg) {
+  for (uint32_t i = threadIdx.x; i < n; i += kMgT) s_seg[i] = src[i];
+  __syncthreads();
+  for (uint32_t w = kSortChunk; w < n; w <<= 1) {
+    unsigned long long v[kMergePer];
+    const uint32_t q0 = threadIdx.x * kMergePer;
+    if (q0 < n) {
+      const uint32_t p0 = q0 - q0 % (2 * w);  // kMergePer divides 2w: one pair of runs
+      const uint32_t na = min(w, n - p0), nb = min(w, n - min(n, p0 + w));
+      const uint32_t d0 = q0 - p0;
+      uint32_t lo = d0 > nb ? d0 - nb : 0u, hi = d0 < na ? d0 : na;
+      const unsigned long long* A = s_seg + p0;
+      const unsigned long long* B = s_seg + p0 + na;
+      while (lo < hi) {
+        const uint32_t i = (lo + hi) >> 1;
+        if (A[i] < B[d0 - i - 1]) lo = i + 1; else hi = i;
+      }
+      uint32_t i = lo, j = d0 - lo;
+      unsigned long long x = i < na ? A[i] : ~0ull, y = j < nb ? B[j] : ~0ull;
+#pragma unroll
+      for (int k = 0; k < kMergePer; ++k) {
+        const bool ta = x < y;
+        v[k] = ta ? x : y;
+        if (ta) {
+          ++i;
+          x = i < na ? A[i] : ~0ull;
+        } else {
+          ++j;
+          y = j < nb ? B[j] : ~0ull;
+        }
+      }
+    }
+    __syncthreads();  // every share is read before any is written
+    if (q0 < n)
+#pragma unroll
+      for (int k = 0; k < kMergePer; ++k)
+        if (q0 + k < n) s_seg[q0 + k] = v[k];
+    __syncthreads();
+  }
+}
+
+// One CTA per list longer than kSortChunk (the items with chunk 0 among
+// the first n_long): its chunks, sorted by the per-tile sort in chunk64,
+// are merged into segments of kMergeSeg entries in shared memory; a longer
+// list's segments are then merged pairwise in rounds between chunk64 and
+// tmp64 in global memory, each thread taking an equal share of every
+// round's outputs (split where it crosses from one pair of runs to the
+// next), with a barrier between rounds.  The records of the merged order
+// are written into the instance list.
+__global__ void __launch_bounds__(kMgT, 2) tile_merge_kernel(const uint2* __restrict__ items,
+                                                          const uint32_t* __restrict__ tstart,
+                                                          unsigned long long* __restrict__ chunk64,
+                                                          unsigned long long* __restrict__ tmp64,
+                                                          uint32_t* __restrict__ out, const Header* hdr) {
+  wait_prior_grid();
+  __shared__ unsigned long long s_seg[kMergeSeg];
+  const uint32_t n_long = hdr->n_long;
+  for (uint32_t it = blockIdx.x; it < n_long; it += gridDim.x) {
+    const uint2 item = items[it];
+    if (item.y != 0) continue;  // uniform over the block
+    const uint32_t s = tstart[item.x], L = tstart[item.x + 1] - s;
+    if (L <= kMergeSeg) {
+      merge_segment(chunk64 + s, L, s_seg);
+      for (uint32_t i = threadIdx.x; i < L; i += kMgT) out[s + i] = (uint32_t)s_seg[i];
+      __syncthreads();  // the segment buffer is free for the block's next list
+      continue;
+    }
+    for (uint32_t s0 = 0; s0 < L; s0 += kMergeSeg) {
+      const uint32_t n = min(kMergeSeg, L - s0);
+      merge_segment(chunk64 + s + s0, n, s_seg);
+      for (uint32_t i = threadIdx.x; i < n; i += kMgT) chunk64[s + s0 + i] = s_seg[i];
+      __syncthreads();
+    }
+    unsigned long long* src = chunk64 + s;
+    unsigned long long* dst = tmp64 + s;
+    const uint32_t share = (L + kMgT - 1) / kMgT;
+    for (uint32_t w = kMergeSeg; w < L; w <<= 1) {
+      const uint32_t q0 = min(L, threadIdx.x * share), q1 = min(L, q0 + share);
+      for (uint32_t q = q0; q < q1;) {
+        const uint32_t p0 = q - q % (2 * w);  // the pair of runs holding output q
+        const uint32_t na = min(w, L - p0), nb = min(w, L - min(L, p0 + w));
+        const uint32_t qe = min(q1, p0 + na + nb);
+        merge_path(src, p0, na, p0 + na, nb, dst, p0, q - p0, qe - p0);
+        q = qe;
+      }
+      __syncthreads();  // the round's outputs are written before the next reads them
+      unsigned long long* t = src;
+      src = dst;
+      dst = t;
+    }
+    for (uint32_t i = threadIdx.x; i < L; i += kMgT) out[s + i] = (uint32_t)src[i];
+    __syncthreads();
+  }
 }
 
 }  // namespace
 
-const uint32_t* sorted_instances(const Layout& L, const char* ws) {
-  return (const uint32_t*)(ws + ((L.tile_passes & 1) ? L.ivB : L.ivA));
-}
+const uint32_t* sorted_instances(const Layout& L, const char* ws) { return (const uint32_t*)(ws + L.ivals); }
 
-// grids of the radix passes (5 resident CTAs per SM: the pass is held to 48
-// registers for it, against 4 CTAs at 64 -- the 64-job mix's sort 1676 ->
-// 1622 us; 6 spilled) and of the emission kernels; each loops over the
-// blocks of work the device counts call for
-constexpr uint32_t kPassGrid = 152 * 5, kEmitGrid = 152 * 8;
-
-cudaError_t launch_tile_order(const Layout& L, char* ws, const Header* hdr, cudaStream_t st) {
-  if (!order_possible(L)) return cudaSuccess;  // the lists cannot be dense: the tiles keep their order
-  const uint32_t* tstart = (const uint32_t*)(ws + L.tstart);
-  uint32_t* order = (uint32_t*)(ws + L.tile_order);
-  if (L.NT <= kOrdSingle) {
-    launch_dependent(tile_order_single_kernel, dim3(1), dim3(kOrdT), 0, st, tstart, L.NT, L.cap, hdr, order);
-    return cudaGetLastError();
-  }
-  uint32_t* totals = (uint32_t*)(ws + L.order_count);  // zeroed at the start of bin_sort
-  const unsigned blocks = (L.NT + kOrdT - 1) / kOrdT;
-  launch_dependent(tile_order_count_kernel, dim3(blocks), dim3(kOrdT), 0, st, tstart, L.NT, L.cap, hdr, totals);
-  launch_dependent(tile_order_place_kernel, dim3(blocks), dim3(kOrdT), 0, st, tstart, L.NT, L.cap, hdr,
-                   (const uint32_t*)totals, totals + kOrdBuckets, order);
-  return cudaGetLastError();
-}
+// grids of the scatter, the per-tile sort and the merge; each loops over
+// the work the device counts call for
+constexpr uint32_t kScatGrid = 152 * 6, kSortGrid = 152 * 8, kMergeGrid = 152 * 2;
+constexpr uint32_t kWalkChunksPerWarp = 2;
 
 cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaStream_t st) {
   (void)cfg;
   Header* hdr = (Header*)(ws + L.header);
+  uint32_t* tstart = (uint32_t*)(ws + L.tstart);
   if (L.R == 0)  // no records: every list is empty (and the tiles keep their order)
-    return cudaMemsetAsync(ws + L.tstart, 0, (size_t)(L.NT + 1) * 4, st);
-  // the per-pass counts are accumulated with atomics: start them at zero
-  cudaError_t e = cudaMemsetAsync(ws + L.hist_d, 0, L.Tfin - L.hist_d, st);
-  if (e != cudaSuccess) return e;
-  const uint32_t* vis = (const uint32_t*)(ws + L.vis_count);
-  uint32_t* vis_prefix = (uint32_t*)(ws + L.vis_prefix);
-  uint32_t* hd = (uint32_t*)(ws + L.hist_d);
-  uint32_t* hi = (uint32_t*)(ws + L.hist_i);
-  uint32_t* icount = (uint32_t*)(ws + L.icount);
-  uint32_t* ghist = (uint32_t*)(ws + L.ghist);  // [4 depth + 3 tile][256]
-  const uint32_t* tiles = (const uint32_t*)(ws + L.tiles);
-  uint32_t* ckA = (uint32_t*)(ws + L.ckA);
-  uint32_t* cvA = (uint32_t*)(ws + L.cvA);
-  uint32_t* ckB = (uint32_t*)(ws + L.ckB);
-  uint32_t* cvB = (uint32_t*)(ws + L.cvB);
-  const bool fuse_vis = L.n_cmp_tiles <= kFusePrefixMax;
-  if (!fuse_vis)
-    launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, vis, vis_prefix, L.n_cmp_tiles, 1, nullptr,
-                     nullptr, 0u, 1u);
-  const size_t hd_stride = (size_t)L.n_dsort_tiles * 256;
-  launch_dependent(compact_kernel, dim3(L.n_cmp_tiles), dim3(kCmpT), 0, st, tiles, (const uint32_t*)(ws + L.key), L.R,
-                   (const uint32_t*)vis_prefix, fuse_vis ? vis : nullptr, ckA, cvA, hd, hdr);
-  // depth sort: 4 passes A->B->A->B->A; the last one counts instances per
-  // emission block
-  for (int p = 0; p < 4; ++p) {
-    const bool even = (p & 1) == 0;
-    uint32_t* hp = hd + p * hd_stride;
-    const bool last = p == 3;
-    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_dsort_tiles, 256, ghist + 256 * p,
-                     (const uint64_t*)&hdr->n_visible, L.R, (uint32_t)kDsTile);
-    launch_dependent(downsweep_kernel<kDsTile>, dim3(min(L.n_dsort_tiles, kPassGrid)), dim3(kOsT), 0, st, even ? ckA : ckB, even ? cvA : cvB, even ? ckB : ckA,
-                                                       even ? cvB : cvA, &hdr->n_visible, L.R, 8 * p, ghist + 256 * p,
-                                                       hp, last ? nullptr : hp + hd_stride, last ? icount : nullptr,
-                                                       tiles);
+    return cudaMemsetAsync(tstart, 0, (size_t)(L.NT + 1) * 4, st);
+  const uint32_t* tcount = (const uint32_t*)(ws + L.tcount);  // zeroed by ubs_preprocess
+  uint32_t* cursor = (uint32_t*)(ws + L.cursor);
+  uint2* items = (uint2*)(ws + L.items);
+  // the tile order's bucket totals and cursors: zero here (zeroed by
+  // ubs_preprocess with the counts, and again by the scatter once used)
+  uint32_t* order_count = (uint32_t*)(ws + L.order_count);
+  uint32_t* order = order_possible(L) ? (uint32_t*)(ws + L.tile_order) : nullptr;
+  // the visibility walk: chunks of mask words sized so that every warp of
+  // the grid has a few (between 1 and 32 words a chunk)
+  uint32_t chunk = L.mask_words / (kWalkChunksPerWarp * kScatGrid * kScatW);
+  chunk = chunk < 1 ? 1 : (chunk > 32 ? 32 : chunk);
+  const uint32_t n_chunks = (L.mask_words + chunk - 1) / chunk;
+  const uint32_t walk_blocks = (n_chunks + kScatW - 1) / kScatW;
+  const dim3 walk_grid(walk_blocks < kScatGrid ? walk_blocks : kScatGrid);
+  launch_dependent(count_kernel, walk_grid, dim3(kScatT), 0, st, (const uint32_t*)(ws + L.tiles),
+                   (const uint2*)(ws + L.rect), (const uint32_t*)(ws + L.vis_mask), L.mask_words, chunk,
+                   (const ViewDev*)(ws + L.views), L.V, L.NT, (uint32_t*)(ws + L.tcount),
+                   (uint32_t*)(ws + L.vis_part));
+  const uint32_t nb = L.n_scan_blocks;
+  ScanPart* part = (ScanPart*)(ws + L.scan_part);
+  launch_dependent(scan_part_kernel, dim3(nb), dim3(kScT), 0, st, tcount, L.NT, part,
+                   order_count, order != nullptr);
+  ScanPart* pre = nullptr;
+  ScanPart* tot = nullptr;
+  if (nb > kFusePrefixMax) {
+    pre = part + nb;
+    tot = part + 2 * nb;
+    launch_dependent(scan_mid_kernel, dim3(1), dim3(kScT), 0, st, (const ScanPart*)part, nb, pre, tot);
   }
-  uint32_t* ikA = (uint32_t*)(ws + L.ikA);
-  uint32_t* ivA = (uint32_t*)(ws + L.ivA);
-  uint32_t* ikB = (uint32_t*)(ws + L.ikB);
-  uint32_t* ivB = (uint32_t*)(ws + L.ivB);
-  const ViewDev* views = (const ViewDev*)(ws + L.views);
-  const bool fuse_icount = L.n_emit_tiles <= kFusePrefixMax;
-  if (!fuse_icount)
-    launch_dependent(col_scan_kernel, dim3(1), dim3(kScT), 0, st, icount, icount, L.n_emit_tiles, 1, nullptr,
-                     (const uint64_t*)&hdr->n_visible, L.R, (uint32_t)kEmTile);
-  uint32_t* ioff = (uint32_t*)(ws + L.ioff);
-  launch_dependent(emit_offsets_kernel, dim3(min(L.n_emit_tiles, kEmitGrid)), dim3(kEmT), 0, st, cvA, tiles,
-                   (const uint32_t*)icount, fuse_icount, ioff, L.cap, hdr);
-  launch_dependent(emit_fill_kernel, dim3(min(L.n_isort_tiles, kEmitGrid)), dim3(kFlT), 0, st, cvA, ioff, (const uint2*)(ws + L.rect), views, L.V, L.cap,
-                                                     ikA, ivA, L.tile_passes > 0 ? hi : nullptr, hdr);
-  uint32_t* gh_tile = ghist + 4 * 256;
-  const size_t hi_stride = (size_t)L.n_isort_tiles * 256;
-  for (int p = 0; p < L.tile_passes; ++p) {
-    const bool even = (p & 1) == 0;
-    uint32_t* hp = hi + p * hi_stride;
-    const bool last = p == L.tile_passes - 1;
-    launch_dependent(col_scan_kernel, dim3(256), dim3(kScT), 0, st, hp, hp, L.n_isort_tiles, 256, gh_tile + 256 * p,
-                     (const uint64_t*)&hdr->n_inst, L.cap, (uint32_t)kIsTile);
-    launch_dependent(downsweep_kernel<kIsTile>, dim3(min(L.n_isort_tiles, kPassGrid)), dim3(kOsT), 0, st, even ? ikA : ikB, even ? ivA : ivB, even ? ikB : ikA,
-                                                       even ? ivB : ivA, &hdr->n_inst, L.cap, 8 * p,
-                                                       gh_tile + 256 * p, hp, last ? nullptr : hp + hi_stride,
-                                                       nullptr, nullptr);
-  }
-  const uint32_t* skeys = (const uint32_t*)(ws + ((L.tile_passes & 1) ? L.ikB : L.ikA));
-  launch_dependent(ranges_kernel, dim3(592), dim3(256), 0, st, skeys, &hdr->n_inst, L.cap, L.NT, (uint32_t*)(ws + L.tstart));
-  return launch_tile_order(L, ws, hdr, st);
-}
-
-void sort_tile_sizes(uint32_t R, uint32_t cap, uint32_t* n_cmp, uint32_t* n_emit, uint32_t* n_dsort,
-                     uint32_t* n_isort) {
-  *n_cmp = (R + kCmpTile - 1) / kCmpTile;
-  *n_emit = (R + kEmTile - 1) / kEmTile;
-  *n_dsort = (R + kDsTile - 1) / kDsTile;
-  *n_isort = (cap + kIsTile - 1) / kIsTile;
+  launch_dependent(scan_place_kernel, dim3(nb), dim3(kScT), 0, st, tcount, L.NT, L.cap, (const ScanPart*)part, nb,
+                   (const ScanPart*)pre, (const ScanPart*)tot, hdr, tstart, cursor, items, order_count, order);
+  uint32_t* bucket = (uint32_t*)(ws + L.bucket);
+  launch_dependent(scatter_kernel, walk_grid, dim3(kScatT), 0, st, (const uint32_t*)(ws + L.tiles),
+                   (const uint2*)(ws + L.rect), (const uint32_t*)(ws + L.vis_mask), L.mask_words, chunk,
+                   (const ViewDev*)(ws + L.views), L.V, L.NT, L.cap, (const Header*)hdr, cursor, bucket,
+                   order_count);
+  uint32_t* out = (uint32_t*)(ws + L.ivals);
+  unsigned long long* chunk64 = (unsigned long long*)(ws + L.chunk64);
+  const uint32_t ts_blocks = (L.max_items + kTsW - 1) / kTsW;
+  launch_dependent(tile_sort_kernel, dim3(ts_blocks < kSortGrid ? ts_blocks : kSortGrid), dim3(kTsW * 32), 0, st,
+                   (const uint2*)items, (const uint32_t*)tstart, (const uint32_t*)(ws + L.key), L.R,
+                   (const uint32_t*)bucket, out, chunk64, hdr);
+  launch_dependent(tile_merge_kernel, dim3(kMergeGrid), dim3(kMgT), 0, st, (const uint2*)items,
+                   (const uint32_t*)tstart, chunk64, (unsigned long long*)(ws + L.tmp64), out, (const Header*)hdr);
+  return cudaGetLastError();
 }
 
 }  // namespace ubs
