@@ -223,9 +223,11 @@ ubs_status ubs_preprocess(const ubs_problem* problem, void* workspace, size_t wo
 
 /* B1-B3: lists every (tile, record) instance, orders each tile's list front
  * to back by (float32 depth, record index) and finds each tile's range.
- * If the instances exceed problem->instance_capacity the device status
- * becomes UBS_ERR_CAPACITY (with the required count) and the lists are left
- * incomplete; later calls on this workspace then do nothing. */
+ * Must follow ubs_preprocess on the same workspace (it reads the records
+ * and visibility that call writes, and the counters it zeroes).  If the
+ * instances exceed problem->instance_capacity the device status becomes
+ * UBS_ERR_CAPACITY (with the required count) and every list is left
+ * empty; later calls on this workspace then do nothing. */
 ubs_status ubs_bin_sort(const ubs_problem* problem, void* workspace, size_t workspace_bytes,
                         cudaStream_t stream);
 
