@@ -98,7 +98,7 @@ ubs_status make_layout(const ubs_problem* pr, Layout& L) {
   L.tiles = take((size_t)L.R * 4);
   L.rect = take((size_t)L.R * 8);
   L.g2d = take((size_t)L.R * kGradFloats * 4);
-  L.tcount = take((size_t)L.NT * kTileSub * 4 + 4 * 132 * 4 + 32 * 32 * 4);
+  L.tcount = take((size_t)L.NT * kTileSub * 4 + 4 * 132 * 4 + kVisBlocks * 4);
   L.order_count = L.tcount + (size_t)L.NT * kTileSub * 4;
   L.vis_part = L.order_count + 4 * 132 * 4;
   L.cursor = take((size_t)L.NT * kTileSub * 4);
@@ -236,7 +236,7 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
   if (e != cudaSuccess) return UBS_ERR_CUDA;
   e = cudaMemsetAsync(w + L.act_count, 0, (size_t)L.S * 4, stream);
   if (e != cudaSuccess) return UBS_ERR_CUDA;
-  e = cudaMemsetAsync(w + L.tcount, 0, (size_t)L.NT * kTileSub * 4 + 4 * 132 * 4 + 32 * 32 * 4, stream);
+  e = cudaMemsetAsync(w + L.tcount, 0, (size_t)L.NT * kTileSub * 4 + 4 * 132 * 4 + kVisBlocks * 4, stream);
   if (e != cudaSuccess) return UBS_ERR_CUDA;
   // view table: per-view constants, tile/record/pixel/mask offsets
   ViewDev* views = (ViewDev*)(w + L.views);
@@ -371,11 +371,12 @@ ubs_status ubs_read_status(const ubs_problem* pr, void* ws, size_t ws_bytes, ubs
     return UBS_ERR_CUDA;
   out->status = (int32_t)h.status;
   out->reserved = 0;
-  uint32_t part[32 * 32];
+  uint32_t part[kVisBlocks];
   if (cudaMemcpy(part, (char*)ws + L.vis_part, sizeof(part), cudaMemcpyDeviceToHost) != cudaSuccess)
     return UBS_ERR_CUDA;
   int64_t vis = 0;
-  for (int i = 0; i < 32; ++i) vis += part[32 * i];
+  const uint32_t nb = L.R ? walk_blocks(L) : 0u;
+  for (uint32_t i = 0; i < nb; ++i) vis += part[i];
   out->visible_records = vis;
   out->instances = (int64_t)h.n_inst;
   return UBS_OK;

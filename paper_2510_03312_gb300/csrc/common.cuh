@@ -87,7 +87,7 @@ struct Layout {
   size_t header, views, rec4, key, tiles, rect, g2d;
   size_t tcount;     // instances per (tile, sub-bucket) [kTileSub][NT], then per length bucket
                      // the totals and cursors of the tile order and of the short lists' sort
-                     // items [4 x 132], then the visible records' partial sums [32 x 32]
+                     // items [4 x 132], then the visible records per count block [kVisBlocks]
                      // (zeroed together by ubs_preprocess)
   size_t cursor;     // next free slot of each (tile, sub-bucket) [kTileSub][NT]
   size_t vis_mask;   // per view, a bit per primitive: visible (written whole by preprocess) [mask_words]
@@ -100,7 +100,7 @@ struct Layout {
   size_t tstart;
   size_t tile_order;   // the order the blend kernels take the tiles in [NT]
   size_t order_count;  // the length buckets' totals and cursors [4 x 132] (after tcount)
-  size_t vis_part;     // visible records in 32 partial sums, 128 bytes apart [32 x 32] (after order_count)
+  size_t vis_part;     // visible records per block of the binning's count walk [kVisBlocks] (after order_count)
   size_t act_list;   // per scene (at the sum of the earlier scenes' P): primitives visible in some view
   size_t act_count;  // their number per scene [kMaxScenes]
   size_t Tfin, last, pairs;
@@ -144,6 +144,7 @@ constexpr uint32_t kScanTiles = 1024;
 constexpr uint32_t kTileSub = 8;
 constexpr uint32_t kSortChunk = 1024;
 constexpr int kCtrSortItems = 8;  // header counter of the per-tile sort's next item
+constexpr uint32_t kVisBlocks = 1024;  // bound on the blocks of the binning's count walk
 
 enum DevStatus : uint32_t { kDevOk = 0, kDevCapacity = 3, kDevTimeout = 5, kDevInternal = 6 };
 

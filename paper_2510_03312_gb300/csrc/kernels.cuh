@@ -115,6 +115,9 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
 // reported by sorted_instances()
 cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaStream_t st);
 const uint32_t* sorted_instances(const Layout& L, const char* ws);
+// blocks of the binning's walks over the visible records (each count block
+// writes its visible records to vis_part[block])
+uint32_t walk_blocks(const Layout& L);
 
 cudaError_t launch_render_fwd(const Layout& L, const CfgDev& cfg, char* ws, float* image, cudaStream_t st);
 cudaError_t launch_render_bwd(const Layout& L, const CfgDev& cfg, char* ws, const float* dL_dimage, cudaStream_t st);

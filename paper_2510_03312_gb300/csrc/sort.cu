@@ -448,17 +448,19 @@ __device__ __forceinline__ void walk_visible(const uint32_t* __restrict__ vis_ma
 }
 
 // B1: every visible record adds one to its sub-bucket (record index mod
-// kTileSub) of each tile of its rectangle, and the visible records are
-// summed into 32 partial sums (global warp id mod 32, 128 bytes apart).
+// kTileSub) of each tile of its rectangle; each block writes the number of
+// visible records it walked to vis_block[block] (overwritten by every
+// binning).
 __global__ void __launch_bounds__(kScatT) count_kernel(const uint32_t* __restrict__ tiles,
                                                        const uint2* __restrict__ rect,
                                                        const uint32_t* __restrict__ vis_mask, uint32_t mask_words,
                                                        uint32_t chunk, const ViewDev* __restrict__ views, int V,
                                                        uint32_t NT, uint32_t* __restrict__ tcount,
-                                                       uint32_t* __restrict__ vis_part) {
+                                                       uint32_t* __restrict__ vis_block) {
   wait_prior_grid();
   __shared__ ViewTable s_vt;
   __shared__ uint32_t s_list[kScatW][32 * 32];
+  __shared__ uint32_t s_vis[kScatW];
   stage_views(s_vt, views, V);
   __syncthreads();
   uint32_t nvis = 0;
@@ -477,24 +479,32 @@ __global__ void __launch_bounds__(kScatT) count_kernel(const uint32_t* __restric
                  });
                });
   const uint32_t w = __reduce_add_sync(kFull, nvis);
-  if (lane_id() == 0 && w) atomicAdd(vis_part + 32 * ((blockIdx.x * kScatW + (threadIdx.x >> 5)) & 31u), w);
+  if (lane_id() == 0) s_vis[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t b = 0;
+    for (int i = 0; i < kScatW; ++i) b += s_vis[i];
+    vis_block[blockIdx.x] = b;
+  }
 }
 
 // Every visible record writes its index into the bucket of each tile of its
 // rectangle, at a slot taken from its sub-bucket's cursor: a lane's own
 // rectangle of up to kSoloTiles tiles with all its adds in flight together,
 // a larger one with all lanes of the warp working on it in turn.  Nothing is
-// written after a capacity overflow.  Block 0 also zeroes the length
-// buckets' totals and cursors, which the scan has used, for the next
-// binning on this workspace.
+// written after a capacity overflow.  The kernel also zeroes the tile
+// counters and the length buckets' totals and cursors, which the scan has
+// used, for the next binning on this workspace.
 __global__ void __launch_bounds__(kScatT) scatter_kernel(const uint32_t* __restrict__ tiles,
                                                          const uint2* __restrict__ rect,
                                                          const uint32_t* __restrict__ vis_mask, uint32_t mask_words,
                                                          uint32_t chunk, const ViewDev* __restrict__ views, int V,
                                                          uint32_t NT, uint32_t cap, const Header* hdr,
                                                          uint32_t* cursor, uint32_t* __restrict__ bucket,
+                                                         uint32_t* __restrict__ tcount,
                                                          uint32_t* __restrict__ order_count) {
   wait_prior_grid();
+  for (uint32_t i = blockIdx.x * kScatT + threadIdx.x; i < kTileSub * NT; i += gridDim.x * kScatT) tcount[i] = 0;
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < 4 * kOrdBuckets; i += kScatT) order_count[i] = 0;
   __shared__ ViewTable s_vt;
@@ -805,6 +815,18 @@ const uint32_t* sorted_instances(const Layout& L, const char* ws) { return (cons
 constexpr uint32_t kScatGrid = 152 * 6, kSortGrid = 152 * 8, kMergeGrid = 152 * 2;
 constexpr uint32_t kWalkChunksPerWarp = 2;
 
+uint32_t walk_chunk(const Layout& L) {
+  const uint32_t chunk = L.mask_words / (kWalkChunksPerWarp * kScatGrid * kScatW);
+  return chunk < 1 ? 1 : (chunk > 32 ? 32 : chunk);
+}
+
+uint32_t walk_blocks(const Layout& L) {
+  const uint32_t chunk = walk_chunk(L);
+  const uint32_t n_chunks = (L.mask_words + chunk - 1) / chunk;
+  const uint32_t blocks = (n_chunks + kScatW - 1) / kScatW;
+  return blocks < kScatGrid ? blocks : kScatGrid;
+}
+
 cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaStream_t st) {
   (void)cfg;
   Header* hdr = (Header*)(ws + L.header);
@@ -820,15 +842,13 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   uint32_t* order = order_possible(L) ? (uint32_t*)(ws + L.tile_order) : nullptr;
   // the visibility walk: chunks of mask words sized so that every warp of
   // the grid has a few (between 1 and 32 words a chunk)
-  uint32_t chunk = L.mask_words / (kWalkChunksPerWarp * kScatGrid * kScatW);
-  chunk = chunk < 1 ? 1 : (chunk > 32 ? 32 : chunk);
-  const uint32_t n_chunks = (L.mask_words + chunk - 1) / chunk;
-  const uint32_t walk_blocks = (n_chunks + kScatW - 1) / kScatW;
-  const dim3 walk_grid(walk_blocks < kScatGrid ? walk_blocks : kScatGrid);
+  const uint32_t chunk = walk_chunk(L);
+  const dim3 walk_grid(walk_blocks(L));
   launch_dependent(count_kernel, walk_grid, dim3(kScatT), 0, st, (const uint32_t*)(ws + L.tiles),
                    (const uint2*)(ws + L.rect), (const uint32_t*)(ws + L.vis_mask), L.mask_words, chunk,
                    (const ViewDev*)(ws + L.views), L.V, L.NT, (uint32_t*)(ws + L.tcount),
                    (uint32_t*)(ws + L.vis_part));
+  static_assert(kVisBlocks >= kScatGrid, "a visible-record count per walk block");
   const uint32_t nb = L.n_scan_blocks;
   ScanPart* part = (ScanPart*)(ws + L.scan_part);
   launch_dependent(scan_part_kernel, dim3(nb), dim3(kScT), 0, st, tcount, L.NT, part,
@@ -846,7 +866,7 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
   launch_dependent(scatter_kernel, walk_grid, dim3(kScatT), 0, st, (const uint32_t*)(ws + L.tiles),
                    (const uint2*)(ws + L.rect), (const uint32_t*)(ws + L.vis_mask), L.mask_words, chunk,
                    (const ViewDev*)(ws + L.views), L.V, L.NT, L.cap, (const Header*)hdr, cursor, bucket,
-                   order_count);
+                   (uint32_t*)(ws + L.tcount), order_count);
   uint32_t* out = (uint32_t*)(ws + L.ivals);
   unsigned long long* chunk64 = (unsigned long long*)(ws + L.chunk64);
   const uint32_t ts_blocks = (L.max_items + kTsW - 1) / kTsW;

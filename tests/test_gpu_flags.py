@@ -100,3 +100,25 @@ def test_checked_mode_reports_an_out_of_range_record_id():
     ws32[base + off + n // 2] = r.R + 5
     r.render_fwd()
     assert r.status().status == U.UBS_OK
+
+
+def test_binning_twice_after_one_preprocess():
+    """ubs_bin_sort reads what ubs_preprocess wrote and leaves its own
+    counters as it found them: a second call on the same workspace gives the
+    same lists, ranges, visible records and instances, and the same image."""
+    scenes, views = _case(3, 91)
+    dev = [raster.DeviceScene.from_scene(s) for s in scenes]
+    r = raster.Rasterizer(dev, views, S.RasterConfig())
+    img = r.forward(check=True).clone()
+    st1 = r.status()
+    n = int(st1.instances)
+    inst1 = r.export(U.EXPORT_INSTANCES)[:n].clone()
+    tstart1 = r.export(U.EXPORT_TILE_START).clone()
+    for _ in range(2):
+        r.bin_sort()
+        st2 = r.status()
+        assert st2.status == U.UBS_OK
+        assert (st2.visible_records, st2.instances) == (st1.visible_records, st1.instances)
+        assert torch.equal(r.export(U.EXPORT_INSTANCES)[:n], inst1)
+        assert torch.equal(r.export(U.EXPORT_TILE_START), tstart1)
+    assert torch.equal(r.render_fwd().clone(), img)
