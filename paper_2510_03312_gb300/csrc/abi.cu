@@ -14,9 +14,17 @@ struct ViewChunk {
   ViewDev v[kUploadChunk];
 };
 
-__global__ void upload_views_kernel(ViewChunk chunk, int n, ViewDev* dst) {
+// Copies a chunk of the view table; the first chunk's launch also zeroes
+// the status header and the per-scene counts of drawn primitives (hdr and
+// act_count non-null).
+__global__ void upload_views_kernel(ViewChunk chunk, int n, ViewDev* dst, uint32_t* hdr, uint32_t hdr_words,
+                                    uint32_t* act_count, int S) {
   const int i = threadIdx.x;
   if (i < n) dst[i] = chunk.v[i];
+  if (hdr) {
+    for (uint32_t k = i; k < hdr_words; k += blockDim.x) hdr[k] = 0;
+    for (int k = i; k < S; k += blockDim.x) act_count[k] = 0;
+  }
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -232,12 +240,7 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
   ubs_status st = prepare(pr, ws, ws_bytes, L);
   if (st != UBS_OK) return st;
   char* w = (char*)ws;
-  cudaError_t e = cudaMemsetAsync(w + L.header, 0, sizeof(Header), stream);
-  if (e != cudaSuccess) return UBS_ERR_CUDA;
-  e = cudaMemsetAsync(w + L.act_count, 0, (size_t)L.S * 4, stream);
-  if (e != cudaSuccess) return UBS_ERR_CUDA;
-  e = cudaMemsetAsync(w + L.tcount, 0, (size_t)L.NT * kTileSub * 4 + 4 * 132 * 4 + kVisBlocks * 4, stream);
-  if (e != cudaSuccess) return UBS_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
   // view table: per-view constants, tile/record/pixel/mask offsets
   ViewDev* views = (ViewDev*)(w + L.views);
   uint32_t tile_off = 0, rec_off = 0, pix_off = 0, mask_off = 0;
@@ -269,17 +272,29 @@ ubs_status ubs_preprocess(const ubs_problem* pr, void* ws, size_t ws_bytes, cuda
       pix_off += (uint32_t)(v.width * v.height);
       mask_off += (uint32_t)((pr->scenes[v.scene_id].P + 31) / 32);
     }
-    upload_views_kernel<<<1, kUploadChunk, 0, stream>>>(chunk, n, views + c0);
+    static_assert(sizeof(Header) % 4 == 0, "the header is zeroed by words");
+    upload_views_kernel<<<1, kUploadChunk, 0, stream>>>(chunk, n, views + c0,
+                                                         c0 == 0 ? (uint32_t*)(w + L.header) : nullptr,
+                                                         (uint32_t)(sizeof(Header) / 4), (uint32_t*)(w + L.act_count),
+                                                         L.S);
     e = cudaGetLastError();
     if (e != cudaSuccess) return UBS_ERR_CUDA;
   }
   const CfgDev cfg = cfg_dev(pr->cfg);
   uint64_t act_off = 0;
+  // the first scene that launches also zeroes the binning's counters (tile
+  // counters, length buckets, visible records per count block); where no
+  // scene launches there are no records and the binning reads none of them
+  bool zeroed = false;
+  const uint32_t nzero = L.NT * kTileSub + 4 * 132 + kVisBlocks;
   for (int s = 0; s < L.S; ++s) {
     ViewList vl;
     view_list(pr, s, vl);
+    const bool launches = pr->scenes[s].P > 0 && vl.n > 0;
+    uint32_t* zero = launches && !zeroed ? (uint32_t*)(w + L.tcount) : nullptr;
+    zeroed = zeroed || launches;
     e = launch_preprocess(scene_dev(pr->scenes[s]), vl, views, cfg, L, w, (uint32_t*)(w + L.act_list) + act_off,
-                          (uint32_t*)(w + L.act_count) + s, stream);
+                          (uint32_t*)(w + L.act_count) + s, zero, zero ? nzero : 0u, stream);
     act_off += (uint64_t)pr->scenes[s].P;
     if (e != cudaSuccess) return UBS_ERR_CUDA;
   }

@@ -108,8 +108,11 @@ struct ViewList {
 
 // act_list/act_count: the scene's list of primitives visible in some view
 // (appended by preprocess, read by the parameter backward)
+// zero/nzero: words the launch zeroes besides its own work (the binning's
+// counters), or none
 cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const ViewDev* views, const CfgDev& cfg,
-                              const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, cudaStream_t st);
+                              const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, uint32_t* zero,
+                              uint32_t nzero, cudaStream_t st);
 
 // scan/sort/emit/ranges; leaves the sorted instance records in the buffer
 // reported by sorted_instances()

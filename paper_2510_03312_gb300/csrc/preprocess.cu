@@ -32,13 +32,21 @@ __device__ __forceinline__ void load_prim(const SceneDev& sc, int64_t p, PrimIn<
   }
 }
 
+// Zeroes zero[0, n) over the grid (the binning's counters, with the first
+// scene's launch).
+__device__ __forceinline__ void zero_words(uint32_t* __restrict__ zero, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) zero[i] = 0;
+}
+
 template <int C>
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev sc, ViewList vl, const ViewDev* __restrict__ views,
                                                          CfgDev cfg, float4* __restrict__ rec4,
                                                          uint32_t* __restrict__ key, uint32_t* __restrict__ tiles,
                                                          uint2* __restrict__ rect, uint32_t* __restrict__ vis_mask,
-                                                         uint32_t* __restrict__ act_list, uint32_t* act_count) {
+                                                         uint32_t* __restrict__ act_list, uint32_t* act_count,
+                                                         uint32_t* __restrict__ zero, uint32_t nzero) {
   wait_prior_grid();
+  zero_words(zero, nzero);
   extern __shared__ ViewDev s_views[];
   for (int i = threadIdx.x; i < vl.n; i += blockDim.x) s_views[i] = views[vl.idx[i]];
   __syncthreads();
@@ -107,8 +115,10 @@ __global__ void __launch_bounds__(256, 3) preprocess_queued_kernel(SceneDev sc, 
                                                                 float4* __restrict__ rec4, uint32_t* __restrict__ key,
                                                                 uint32_t* __restrict__ tiles, uint2* __restrict__ rect,
                                                                 uint32_t* __restrict__ vis_mask,
-                                                                uint32_t* __restrict__ act_list, uint32_t* act_count) {
+                                                                uint32_t* __restrict__ act_list, uint32_t* act_count,
+                                                                uint32_t* __restrict__ zero, uint32_t nzero) {
   wait_prior_grid();
+  zero_words(zero, nzero);
   extern __shared__ ViewDev s_views[];
   // per warp: the lanes' view-independent values (mean, Sigma, beta_x, rgb),
   // and the queue (record, view | owner lane << 16, shift, o(q))
@@ -239,7 +249,8 @@ cudaError_t prepare_queued() {
 }
 
 cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const ViewDev* views, const CfgDev& cfg,
-                              const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, cudaStream_t st) {
+                              const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, uint32_t* zero,
+                              uint32_t nzero, cudaStream_t st) {
   if (sc.P == 0 || vl.n == 0) return cudaSuccess;
   if (sc.N > 3) {
     const cudaError_t e = prepare_queued();
@@ -254,10 +265,10 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
   uint2* rect = (uint2*)(ws + L.rect);
   uint32_t* vis = (uint32_t*)(ws + L.vis_mask);
   switch (sc.N) {
-    case 3: launch_dependent(preprocess_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
-    case 4: launch_dependent(preprocess_queued_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
-    case 6: launch_dependent(preprocess_queued_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
-    case 7: launch_dependent(preprocess_queued_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count); break;
+    case 3: launch_dependent(preprocess_kernel<0>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count, zero, nzero); break;
+    case 4: launch_dependent(preprocess_queued_kernel<1>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count, zero, nzero); break;
+    case 6: launch_dependent(preprocess_queued_kernel<3>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count, zero, nzero); break;
+    case 7: launch_dependent(preprocess_queued_kernel<4>, dim3(blocks), dim3(threads), smem, st, sc, vl, views, cfg, rec4, key, tiles, rect, vis, act_list, act_count, zero, nzero); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
