@@ -219,6 +219,31 @@ def test_very_long_tile_lists():
     assert n_cmp > 0 and total > 0
 
 
+def test_equal_depths_keep_record_order():
+    """16,000 primitives on one plane parallel to the image plane, so that
+    every visible record has the same float32 depth: each tile's list must
+    come out in record order (Sec. 3's front-to-back order, the record index
+    breaking ties), bit for bit, although the binning's buckets are filled
+    in the order its atomic adds happen to run.  The longest lists (over
+    6,000 entries) go through the chunked sort and both kinds of merge."""
+    rng = np.random.default_rng(67)
+    sc = S.make_scene(67, 3, 16000, means="uniform", extent=0.3, scale_range=(0.02, 0.06), rng=rng)
+    sc.plane("mean_x")[2] = 0.0
+    v = S.View(R=np.eye(3, dtype=np.float32), t=np.array([0, 0, 3], np.float32), fx=120.0, fy=120.0,
+               cx=48.0, cy=40.0, width=96, height=80)
+    cfg = S.RasterConfig()
+    orc = R64.Oracle([sc], [v], cfg)
+    pre = orc.pre32[0]
+    vis = pre["valid"] & (pre["tiles_touched"] > 0)
+    assert vis.sum() > 15000 and np.unique(pre["depth_bits"][vis]).size == 1
+    counts = np.diff(orc.bins["ranges"], axis=1)[:, 0]
+    assert counts.max() > 4096
+    gpu = gpu_forward([sc], [v], cfg)
+    recs = check_preprocess(gpu, orc)
+    check_bins(gpu, orc)
+    check_images(gpu, orc, recs=recs, tiles=sorted(np.argsort(-counts)[:2].tolist()))
+
+
 def _deep_tile_case(split):
     sc = S.make_scene(65, 3, 24000, means="uniform", extent=0.04, scale_range=(0.01, 0.04))
     R, t = S.look_at((0.0, 0.0, -3.0))
