@@ -13,7 +13,9 @@ import pytest
 import torch
 
 from oracle import render64 as R64
+from paper_2510_03312_gb300 import raster
 from paper_2510_03312_gb300 import scenes as S
+from paper_2510_03312_gb300 import ubs as U
 
 from parity_tools import check_bins, check_grads, check_images, check_pairs, check_preprocess, gpu_forward
 
@@ -242,6 +244,30 @@ def test_equal_depths_keep_record_order():
     recs = check_preprocess(gpu, orc)
     check_bins(gpu, orc)
     check_images(gpu, orc, recs=recs, tiles=sorted(np.argsort(-counts)[:2].tolist()))
+
+
+def test_binning_over_two_million_tiles():
+    """17 views of 4096x2048 at 8x8 tiles: 2,228,224 tiles, more than the
+    2048 x 1024 the binning's scan covers in two kernels, so its middle
+    kernel scans the blocks' sums in between.  Instance lists and tile
+    ranges bit-exact against the oracle."""
+    rng = np.random.default_rng(68)
+    sc = S.make_scene(68, 3, 3000, means="uniform", extent=1.0, rng=rng)
+    views = S.sphere_views(rng, 17, 4.0, 4096, 2048)
+    cfg = S.RasterConfig(tile_w=8, tile_h=8)
+    n_tiles = 17 * (4096 // 8) * (2048 // 8)
+    assert (n_tiles + 1023) // 1024 > 2048
+    orc = R64.Oracle([sc], views, cfg)
+    r = raster.Rasterizer([raster.DeviceScene.from_scene(sc)], views, cfg)
+    r.forward(check=True)
+    st = r.status()
+    n = int(st.instances)
+    assert n > 10000
+    gpu = {"status": st,
+           "instances": r.export(U.EXPORT_INSTANCES).cpu().numpy().view(np.uint32)[:n],
+           "tstart": r.export(U.EXPORT_TILE_START).cpu().numpy().view(np.uint32)}
+    assert gpu["tstart"].size == n_tiles + 1
+    check_bins(gpu, orc)
 
 
 def _deep_tile_case(split):
