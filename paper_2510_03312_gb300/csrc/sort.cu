@@ -29,7 +29,10 @@
 //
 // No kernel waits on another block: every step's inputs are made by the
 // kernels before it.  A work item of the per-tile sort holds at most
-// kSortChunk entries, so the items need no ordering to balance the grid.
+// kSortChunk entries; the warps take the items from a counter, the long
+// lists' chunks first and then the short lists longest first.  The scatter
+// zeroes the counters the scan has used, so that the binning can run again
+// on the same preprocess.
 #include "kernels.cuh"
 
 namespace ubs {
