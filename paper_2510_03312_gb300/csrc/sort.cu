@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(kScT) scan_place_kernel(const uint32_t* __rest
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    hdr->ctr[kCtrSortItems] = 0;  // the per-tile sort's item counter
+    hdr->ctr[kCtrSortItems] = 0;  // the per-tile sort's and the merge's item counters
+    hdr->ctr[kCtrMergeItems] = 0;
     tstart[NT] = over ? 0u : (uint32_t)T.inst;
     hdr->n_inst = T.inst;
     hdr->n_long = over ? 0u : T.n_long;
@@ -756,7 +757,7 @@ __device__ __forceinline__ void merge_segment(const unsigned long long* __restri
 }
 
 // One CTA per list longer than kSortChunk (the items with chunk 0 among
-// the first n_long): its chunks, sorted by the per-tile sort in chunk64,
+// the first n_long, taken from a counter): its chunks, sorted by the per-tile sort in chunk64,
 // are merged into segments of kMergeSeg entries in shared memory; a longer
 // list's segments are then merged pairwise in rounds between chunk64 and
 // tmp64 in global memory, each thread taking an equal share of every
@@ -767,11 +768,19 @@ __global__ void __launch_bounds__(kMgT, 2) tile_merge_kernel(const uint2* __rest
                                                           const uint32_t* __restrict__ tstart,
                                                           unsigned long long* __restrict__ chunk64,
                                                           unsigned long long* __restrict__ tmp64,
-                                                          uint32_t* __restrict__ out, const Header* hdr) {
+                                                          uint32_t* __restrict__ out, Header* hdr) {
   wait_prior_grid();
   __shared__ unsigned long long s_seg[kMergeSeg];
+  __shared__ uint32_t s_it;
   const uint32_t n_long = hdr->n_long;
-  for (uint32_t it = blockIdx.x; it < n_long; it += gridDim.x) {
+  for (;;) {
+    // the next chunk item, from a counter: the CTAs stay busy however the
+    // long lists fall among them; a list's first chunk stands for the list
+    __syncthreads();  // every thread has read the previous s_it
+    if (threadIdx.x == 0) s_it = atomicAdd(&hdr->ctr[kCtrMergeItems], 1u);
+    __syncthreads();
+    const uint32_t it = s_it;
+    if (it >= n_long) break;
     const uint2 item = items[it];
     if (item.y != 0) continue;  // uniform over the block
     const uint32_t s = tstart[item.x], L = tstart[item.x + 1] - s;
@@ -877,7 +886,7 @@ cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaSt
                    (const uint2*)items, (const uint32_t*)tstart, (const uint32_t*)(ws + L.key), L.R,
                    (const uint32_t*)bucket, out, chunk64, hdr);
   launch_dependent(tile_merge_kernel, dim3(kMergeGrid), dim3(kMgT), 0, st, (const uint2*)items,
-                   (const uint32_t*)tstart, chunk64, (unsigned long long*)(ws + L.tmp64), out, (const Header*)hdr);
+                   (const uint32_t*)tstart, chunk64, (unsigned long long*)(ws + L.tmp64), out, hdr);
   return cudaGetLastError();
 }
 
