@@ -122,7 +122,7 @@ __device__ __forceinline__ void block_excl_scan2(unsigned long long a, uint32_t 
 
 // ---------------------------------------------------------------- tile order
 
-constexpr int kOrdT = 1024, kOrdBuckets = 4 * 33;
+constexpr int kOrdBuckets = 4 * 33;
 
 // bucket of a list length: four per octave, longest first (bucket 0)
 __device__ __forceinline__ int length_bucket(uint32_t n) {
@@ -665,17 +665,6 @@ __global__ void __launch_bounds__(kTsW * 32, 5) tile_sort_kernel(const uint2* __
 // ---------------------------------------------------------------- merge
 
 constexpr int kMgT = 512;  // threads of a merge CTA
-
-// The first position p in [lo, hi) of the sorted keys a[] with a[p] >= x
-// (hi if none).
-__device__ __forceinline__ uint32_t lower_bound64(const unsigned long long* __restrict__ a, uint32_t lo, uint32_t hi,
-                                                  unsigned long long x) {
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 // Merges the sorted runs A = src[a0, a0 + na) and B = src[b0, b0 + nb)
 // (distinct keys) into dst[o0, o0 + na + nb), writing only the outputs
