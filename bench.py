@@ -221,11 +221,12 @@ def kernels_per_step(r):
 
 
 def step_rooflines(stage_ms, names, params_bytes, R, instances, NT, pairs, pk, n_sm):
-    """Every stage against its bound, with the algorithmic work per unit of
-    the design notes: preprocess reads the parameters once and writes 44 B
-    per record; the sort moves 12 B per instance for emission, 24 B per
-    instance per pass of an LSD sort over (tile, depth) keys
-    (ceil((tile bits + 32) / 8) passes) and 8 B per instance for the ranges;
+    """Every stage against its bound, with a fixed algorithmic work per
+    unit: preprocess reads the parameters once and writes 44 B per record;
+    the sort is charged the bytes of an LSD sort of (tile, depth) keys, a
+    reference count the binning itself does not move (12 B per instance to
+    emit the keys, 24 B per instance per pass, ceil((tile bits + 32) / 8)
+    passes, and 8 B per instance for the ranges);
     the forward blend costs 16 FP32 + 2 MUFU operations per pair, the
     backward blend 45 FP32 + 3 MUFU; the parameter backward reads the
     parameters and 40 B of screen gradients per record and writes the
