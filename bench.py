@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd megapixels/sec and views/sec at 1 GB300, batched vs per-view; % of roofline"
 L2_BYTES = 129 * 2 ** 20
 
-# per-pair algorithmic work of the blend kernels (FP32 lane operations; the
-# MUFU operations are bounded separately, see the design notes)
+# per-pair algorithmic work of the blend kernels: FP32 lane operations and,
+# separately, MUFU operations (exp, reciprocal), whose pipe is 8x narrower
 FWD_FP32_PER_PAIR, FWD_MUFU_PER_PAIR = 16, 2
 BWD_FP32_PER_PAIR, BWD_MUFU_PER_PAIR = 45, 3
 # training step: the image loss reads the image and the target and writes

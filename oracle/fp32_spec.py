@@ -32,8 +32,9 @@ The quantities follow the paper: Sec. 4.2 (L, Sigma blocks), Sec. 4.3
 (beta_x = 4 exp(b_x), beta_q = exp(b_q), clamped beta, conditional mean and
 covariance, modulated opacity with d_i = tanh(d_i^raw)), Sec. 3 (EWA
 projection Sigma' = J W Sigma W^T J^T, Mahalanobis r, compact support r < 1).
-Rasterizer constants and the tight cut radius are the readings listed in the
-design notes (3DGS practice).
+Rasterizer constants (alpha_min = 1/255, alpha_max = 0.99, transmittance stop
+1e-4, the 0.3 low-pass dilation) and the tight cut radius follow standard
+3DGS practice, which the paper's rasterizer inherits without restating.
 
 Parity: pinned.  Each float output is compared against the float64
 definition in ``render64`` (tests/test_oracle_fp32_spec.py), exp/log against
