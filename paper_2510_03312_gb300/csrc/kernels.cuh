@@ -114,8 +114,8 @@ cudaError_t launch_preprocess(const SceneDev& sc, const ViewList& vl, const View
                               const Layout& L, char* ws, uint32_t* act_list, uint32_t* act_count, uint32_t* zero,
                               uint32_t nzero, cudaStream_t st);
 
-// scan/sort/emit/ranges; leaves the sorted instance records in the buffer
-// reported by sorted_instances()
+// count, scan (ranges), scatter, per-tile sort and merge; leaves the sorted
+// instance records in the buffer reported by sorted_instances()
 cudaError_t launch_bin_sort(const Layout& L, const CfgDev& cfg, char* ws, cudaStream_t st);
 const uint32_t* sorted_instances(const Layout& L, const char* ws);
 // blocks of the binning's walks over the visible records (each count block
