@@ -142,7 +142,7 @@ constexpr int kGradFloats = 12;
 // then merged)
 constexpr uint32_t kScanTiles = 1024;
 constexpr uint32_t kTileSub = 8;
-constexpr uint32_t kSortChunk = 1024;
+constexpr uint32_t kSortChunk = 512;
 constexpr int kCtrSortItems = 8;   // header counter of the per-tile sort's next item
 constexpr int kCtrMergeItems = 9;  // and of the merge's
 constexpr uint32_t kVisBlocks = 1024;  // bound on the blocks of the binning's count walk

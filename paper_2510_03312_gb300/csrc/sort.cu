@@ -625,14 +625,14 @@ __device__ __forceinline__ void warp_sort_list(const uint32_t* __restrict__ src,
 }
 
 constexpr int kTsW = 4;  // warps per CTA of the per-tile sort
-static_assert(kSortChunk == 32 * 32, "the widest warp sort holds 32 keys a lane");
+static_assert(kSortChunk == 32 * 16, "the widest warp sort holds 16 keys a lane");
 
 // One warp per work item, taken in order from a counter: a list of at most
 // kSortChunk entries is sorted
 // from its bucket into the instance lists; a chunk of a longer list into
 // chunk64 as keys, for the merge.  The warp takes the narrowest network
-// that holds the entries (2, 8, 16 or 32 a lane).
-__global__ void __launch_bounds__(kTsW * 32, 5) tile_sort_kernel(const uint2* __restrict__ items,
+// that holds the entries (2, 8 or 16 a lane).
+__global__ void __launch_bounds__(kTsW * 32, 8) tile_sort_kernel(const uint2* __restrict__ items,
                                                               const uint32_t* __restrict__ tstart,
                                                               const uint32_t* __restrict__ key, uint32_t R,
                                                               const uint32_t* __restrict__ bucket,
@@ -657,8 +657,7 @@ __global__ void __launch_bounds__(kTsW * 32, 5) tile_sort_kernel(const uint2* __
     unsigned long long* o64 = whole ? nullptr : chunk64 + base;
     if (n <= 64) warp_sort_list<2>(bucket + base, n, key, R, o32, o64);
     else if (n <= 256) warp_sort_list<8>(bucket + base, n, key, R, o32, o64);
-    else if (n <= 512) warp_sort_list<16>(bucket + base, n, key, R, o32, o64);
-    else warp_sort_list<32>(bucket + base, n, key, R, o32, o64);
+    else warp_sort_list<16>(bucket + base, n, key, R, o32, o64);
   }
 }
 
